@@ -1,0 +1,195 @@
+/*
+ * pwqt.h -- C ABI of libpwqt: the per-energy open-boundary solve of the
+ * partition-of-unity Bloch-wave method (Van de Put, Fischetti, Vandenberghe,
+ * arXiv:1903.00548) on one GB300 GPU.
+ *
+ * Conventions (all entry points):
+ *  - Every function returns an int status: PWQT_OK (0) or a negative PWQT_ERR_*
+ *    code; pwqt_last_error(ctx) returns a message for the last failure.
+ *  - Complex numbers are interleaved double[2] (re, im).  Matrices are row-major.
+ *  - Host arrays are owned by the caller and only read or written during the
+ *    call; the library never keeps a pointer to them and never returns memory
+ *    that the caller must free.
+ *  - Device state (intrinsic blocks, per-node extrinsic blocks, the cache of
+ *    contact self-energies, factor panels) is owned by the opaque context and
+ *    released by pwqt_destroy.
+ *  - Units: eV for energies and potentials, nm for lengths.
+ *  - A context is thread-compatible, not thread-safe: use one host thread per
+ *    context.  Every computation runs in the library's CUDA kernels (and the
+ *    cuSOLVER/cuBLAS calls named below) on the context's device; there is no
+ *    CPU fallback: without a usable CUDA device pwqt_create fails.
+ */
+#ifndef PWQT_H
+#define PWQT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pwqt_ctx pwqt_ctx;
+
+/* return codes */
+#define PWQT_OK                   0
+#define PWQT_ERR_INVALID_ARG     -1   /* a pointer is NULL, a size is out of range */
+#define PWQT_ERR_BASIS_TOO_SMALL -2   /* fewer plane waves than requested bands    */
+#define PWQT_ERR_OOM             -3   /* device allocation or HBM budget exceeded  */
+#define PWQT_ERR_CUDA            -4   /* a CUDA runtime / library call failed      */
+#define PWQT_ERR_STATE           -5   /* call order violated (e.g. no basis yet)   */
+#define PWQT_ERR_NO_DEVICE       -6   /* no CUDA device / driver                   */
+
+/* per-result status bits (pwqt_solve `status` output) */
+#define PWQT_ST_OK               0
+#define PWQT_ST_SINGULAR_PIVOT   1    /* a pivot of a node block was exactly zero   */
+#define PWQT_ST_MODE_COUNT       2    /* out-flow mode count != n at a contact     */
+#define PWQT_ST_IR_NO_CONVERGE   4    /* refinement hit its iteration limit        */
+#define PWQT_ST_DEGENERATE       8    /* degenerate traveling modes at a contact   */
+#define PWQT_ST_NEAR_UNIT        16   /* an evanescent |lambda| within 1e-5 of 1   */
+
+/* precision of the block sweep */
+#define PWQT_FP64                0    /* complex128 throughout                     */
+#define PWQT_MIXED               1    /* complex64 factorisation on the tensor
+                                         cores (3xTF32 products, FP32 accumulate)
+                                         + refinement with FP64 residuals          */
+
+typedef struct {
+    int    device;             /* CUDA device ordinal                              */
+    size_t hbm_budget_bytes;   /* 0: use 90 % of the free device memory            */
+    double ir_tol;             /* mixed path: stop when ||B - A c|| <= ir_tol ||B||
+                                  (max over columns); 0 -> 1e-12                    */
+    int    ir_max_iters;       /* mixed path refinement limit; 0 -> 40              */
+    int    batch;              /* energies per sweep launch; 0 -> from the budget   */
+} pwqt_opts;
+
+/* One periodic supercell (paper Sec. 2.1, Fig. structure). */
+typedef struct {
+    int           dim;        /* 1: chain along z; 2: ribbon in the x-z plane      */
+    double        Lz;         /* supercell length along transport (nm)             */
+    double        Lx;         /* transverse supercell width (nm); 1 for dim == 1    */
+    int           n_atoms;
+    const double* atoms;      /* n_atoms x 2 (x, z) positions, nm                  */
+    double        omega0;     /* reference volume per atom of the form factor      */
+} pwqt_cell;
+
+/* Local empirical pseudopotential v(q) = v0 exp(-q^2 / (2 sigma^2))
+   (Sec. 2.1, Eq. local_epp; Sec. 1: V(q) a continuous function of q). */
+typedef struct {
+    double v0;                /* eV    */
+    double sigma;             /* nm^-1 */
+} pwqt_formfactor;
+
+/* Create a context on opts->device (NULL: defaults, device 0).
+   Errors: PWQT_ERR_NO_DEVICE, PWQT_ERR_CUDA, PWQT_ERR_INVALID_ARG (out NULL). */
+int pwqt_create(pwqt_ctx** out, const pwqt_opts* opts);
+
+/* Release all device state of the context.  NULL is accepted. */
+int pwqt_destroy(pwqt_ctx* ctx);
+
+/* Message of the last failing call on this context (static storage of ctx). */
+const char* pwqt_last_error(const pwqt_ctx* ctx);
+
+/*
+ * Intrinsic blocks from the pseudopotential (Sec. 2.2-2.3, App. A).
+ * Builds the plane-wave EPM Hamiltonian H_GG' = hbar^2/2m |k+G|^2 delta +
+ * V_{G-G'} (plane waves |k+G| <= gcut; V_G = (omega0/Omega) v(|G|) sum_a
+ * e^{-iG.R_a}, V_0 = 0) at k = 0 and k = pi/Lz, keeps the n_bands lowest Bloch
+ * waves of each (n = 2 n_bands enhancement functions per node, Eq.
+ * wavef_expansion), and forms the element integrals M, H^c = (eps+eps')/2 M +
+ * T + P (Eq. hc_matel_herm) and the extrinsic weights W (Sec. 2.3) in closed
+ * form.  Resets all systems and the self-energy cache.
+ *   n_out: receives n.
+ * Errors: PWQT_ERR_BASIS_TOO_SMALL if a k-point has fewer than n_bands plane
+ * waves; PWQT_ERR_INVALID_ARG; PWQT_ERR_CUDA (cuSOLVER Hermitian eigensolver).
+ */
+int pwqt_assemble_intrinsic(pwqt_ctx* ctx, const pwqt_cell* cell, const pwqt_formfactor* ff,
+                            double gcut, int n_bands, int* n_out);
+
+/*
+ * Same as pwqt_assemble_intrinsic, but with caller-supplied Bloch waves
+ * (Sec. 2.2: "Bloch-wave solutions ... obtained ... using the appropriate
+ * plane-wave basis").  Group g = 0 is k = 0, g = 1 is k = pi/Lz.
+ *   eps   : 2*n_bands band energies, group 0 first.
+ *   n_pw  : 2 counts of plane waves.
+ *   mx, mz: n_pw[0] + n_pw[1] integer plane-wave indices, G = (2 pi mx/Lx, 2 pi mz/Lz).
+ *   coef  : complex, group 0 then group 1, each n_pw[g] x n_bands row-major,
+ *           normalised to sum_G |c|^2 = 1 per band.
+ */
+int pwqt_set_enhancement(pwqt_ctx* ctx, const pwqt_cell* cell, int n_bands, const double* eps,
+                         const int* n_pw, const int* mx, const int* mz, const double* coef,
+                         int* n_out);
+
+/*
+ * Copies of the intrinsic node blocks (Eq. infinite_system), each n x n complex:
+ * H0 = H_ii, H1 = H_{i,i+1}, M0 = M_ii, M1 = M_{i,i+1}, and W (6 blocks:
+ * W^l_ll, W^l_lr, W^l_rr, W^r_ll, W^r_lr, W^r_rr).  Any pointer may be NULL.
+ */
+int pwqt_get_blocks(pwqt_ctx* ctx, double* H0, double* H1, double* M0, double* M1, double* W);
+
+/*
+ * Extrinsic potential of system `sys` (0 <= sys < 64): U_nodes[i] is the
+ * potential energy at node i+1 (i < n_nodes), interpolated by the hats,
+ * V_e(z) = sum_j U_j f_j(z) (Sec. 2.3 V^e elements); the leads are flat at
+ * U_nodes[0] and U_nodes[n_nodes-1].  Builds the per-node blocks H_ii + V_ii
+ * and H_{i,i+1} + V_{i,i+1} on the device.  n_nodes >= 2.
+ */
+int pwqt_set_extrinsic(pwqt_ctx* ctx, int sys, int n_nodes, const double* U_nodes);
+
+/*
+ * Solve [E M - H - Sigma] c = B (Eq. qtbm_system) for every injected mode at
+ * each of the n_E energies of system `sys`, and reduce to observables.
+ * Self-energies (Sec. 3.1: complex bands of the flat leads from the symmetric
+ * linearisation, Eq. linearized_eigenvalue_symmetric; velocities, Eq.
+ * hellmann-feynman; normalisation, Eq. normalization) come from the context's
+ * cache, keyed by E - U_lead, and are computed on a miss (cuSOLVER non-Hermitian
+ * eigensolver + the library's kernels, FP64).
+ * Outputs (host, caller-owned, any may be NULL):
+ *   T      [n_E]        sum over source-injected modes of T_gamma (Eq. transmission)
+ *   R      [n_E]        sum of the source reflection coefficients
+ *   T_ds   [n_E]        drain -> source transmission
+ *   n_open [2*n_E]      injected traveling modes (source, drain)
+ *   node_n [n_E*N*2]    node density per contact, g_gamma sum_alpha |c|^2 (Sec. 3.3)
+ *   resid  [n_E]        final max-column ||B - A c|| / ||B|| (FP64 residual)
+ *   iters  [n_E]        refinement iterations (0 on the FP64 path)
+ *   status [n_E]        PWQT_ST_* bits
+ */
+int pwqt_solve(pwqt_ctx* ctx, int sys, int n_E, const double* E, int precision,
+               double* T, double* R, double* T_ds, int* n_open, double* node_n,
+               double* resid, int* iters, int* status);
+
+/*
+ * pwqt_solve on device buffers: E (n_E doubles) and every output are device
+ * pointers (any output may be NULL), the work is ordered on `stream`
+ * (a cudaStream_t, NULL = the legacy default stream) and the call returns once
+ * it is enqueued and the self-energy cache holds every needed entry (cache
+ * misses are computed synchronously first).  The buffers must stay valid until
+ * the stream reaches the end of the work.
+ */
+int pwqt_solve_dev(pwqt_ctx* ctx, int sys, int n_E, const double* E_host, int precision,
+                   double* T, double* R, double* T_ds, int* n_open, double* node_n,
+                   double* resid, int* iters, int* status, void* stream);
+
+/*
+ * Pre-fill the self-energy cache for energies E - U_lead of system `sys`
+ * (both leads), so that a later pwqt_solve runs with resident self-energies.
+ */
+int pwqt_prepare_leads(pwqt_ctx* ctx, int sys, int n_E, const double* E);
+
+/* Number of cached contact entries and the device bytes they hold. */
+int pwqt_cache_info(pwqt_ctx* ctx, int* entries, size_t* bytes);
+
+/*
+ * Band reconstruction (Sec. 5.1): eigenvalues of H(k') c = E M(k') c with
+ * H(k') = H_ii + H_{i,i+1} e^{ik'Lz} + H_{i,i-1} e^{-ik'Lz}; E_out is n_k x n,
+ * ascending per k'.
+ */
+int pwqt_bands(pwqt_ctx* ctx, int n_k, const double* k, double* E_out);
+
+/* Launch counters of the library's own kernels since the last reset. */
+int pwqt_kernel_launches(pwqt_ctx* ctx, long long* count, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PWQT_H */

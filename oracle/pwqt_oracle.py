@@ -39,7 +39,10 @@ reason in the design notes):
     "-hbar^2/m ... + h.c." of Sec. 2.3 is read as that symmetrised sum.
   * lambda is the ratio (outside neighbour)/(edge node); drain lambda_d =
     c_{i+1}/c_i, source lambda_s = c_{i-1}/c_i = 1/lambda_d with the same c.
-  * traveling iff ||lambda| - 1| < 1e-8.
+  * traveling iff ||lambda| - 1| < 1e-6 on the generalised-QZ eigenvalues;
+    each traveling mode is then refined on the unit circle (Newton on k with
+    the band structure of Sec. 5.1 and the Hellmann-Feynman slope), so that
+    |lambda| = 1 holds to rounding as Sec. 3.1 states for exact arithmetic.
   * degenerate traveling modes are made flux-orthogonal by diagonalising the
     velocity form in the M(lambda) metric.
   * V_e(z) = sum_j U_j f_j(z) (hat interpolation of node potentials); leads
@@ -58,7 +61,7 @@ import numpy as np
 import scipy.linalg as sla
 
 HB2M = 0.0380998212          # hbar^2/(2 m_e), eV nm^2
-TRAVEL_TOL = 1e-8            # ||lambda| - 1| below which a mode is traveling
+TRAVEL_TOL = 1e-6            # ||lambda| - 1| below which a mode is traveling
 DEGEN_TOL = 1e-8             # |lambda_a - lambda_b| below which traveling modes are degenerate
 
 
@@ -318,6 +321,34 @@ def _velocity_form(Kp, Km, lam, L):
     return 1j * L * (lam * Kp - Km / lam)
 
 
+def refine_traveling(blk, Ec: float, lam, c, iters: int = 8):
+    """Put a traveling mode exactly on the unit circle: with lambda = e^{ikL},
+    E(k) is an eigenvalue of H(k) c = E M(k) c (Sec. 5.1); Newton on k with the
+    slope dE/dk of Eq. hellmann-feynman until E(k) = Ec, the eigenvector of the
+    band closest to Ec from scipy's Hermitian-definite eigensolver."""
+    L = blk["L"]
+    k = float(np.angle(lam)) / L
+    best = None
+    for _ in range(iters):
+        ph = np.exp(1j * k * L)
+        Hk = blk["H0"] + blk["H1"] * ph + blk["H1"].conj().T / ph
+        Mk = _m_lambda(blk, ph)
+        Hk, Mk = 0.5 * (Hk + Hk.conj().T), 0.5 * (Mk + Mk.conj().T)
+        w, V = sla.eigh(Hk, Mk)
+        # the band whose eigenvector overlaps most with the current mode
+        ov = np.abs(V.conj().T @ (Mk @ c))
+        b = int(np.argmax(ov / np.sqrt(np.abs(np.einsum("ij,ij->j", V.conj(), Mk @ V)))))
+        c = V[:, b] * (np.vdot(V[:, b], c) / abs(np.vdot(V[:, b], c)))
+        # dE/dk of that band at k (Eq. hellmann-feynman with E = w[b])
+        Kb = blk["H1"] - w[b] * blk["M1"]
+        slope = (np.vdot(c, _velocity_form(Kb, Kb.conj().T, ph, L) @ c) / np.vdot(c, Mk @ c)).real
+        best = (ph, c / np.linalg.norm(c))
+        if abs(w[b] - Ec) < 1e-14 * max(1.0, abs(Ec)) or slope == 0.0:
+            break
+        k -= (w[b] - Ec) / slope
+    return best
+
+
 def lead_modes(blk, Ec: float) -> LeadModes:
     """Complex band structure at energy Ec of the flat lead (Eqs. complex_bs and
     linearized_eigenvalue_symmetric): the 2n x 2n pencil
@@ -337,6 +368,8 @@ def lead_modes(blk, Ec: float) -> LeadModes:
     C /= np.linalg.norm(C, axis=0)[None, :]
     absl = np.abs(lam)
     trav = np.abs(absl - 1.0) < TRAVEL_TOL
+    for j in np.flatnonzero(trav):
+        lam[j], C[:, j] = refine_traveling(blk, Ec, lam[j], C[:, j])
     dEdk = np.zeros(2 * n)
     # degenerate traveling sets: diagonalise the velocity form in the M metric
     idx = np.flatnonzero(trav)
