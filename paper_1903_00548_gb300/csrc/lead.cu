@@ -1,0 +1,446 @@
+// Contact self-energies from the complex band structure of the flat leads
+// (Sec. 3.1-3.2 of arXiv:1903.00548), FP64 on the GPU.
+//
+//  1. The symmetric linearisation (Eq. linearized_eigenvalue_symmetric)
+//        A x = lambda B x,  A = [[K0, K-], [K+, 0]],  B = [[-K+, 0], [0, K+]],
+//     K(E) = H - E M, is brought to standard form by the Cayley transform
+//        C = (A + B)^-1 (A - B),  C x = mu x  <=>  A x = lambda B x with
+//        lambda = (1 + mu)/(1 - mu),
+//     which keeps the transformed spectrum bounded when lambda spans many decades,
+//     and C is diagonalised by cuSOLVER's non-Hermitian eigensolver.
+//  2. Modes with ||lambda| - 1| < 1e-6 are traveling; each is refined onto the unit
+//     circle: with lambda = e^{ikL}, Ec is an eigenvalue of H(k) c = E M(k) c, so
+//     Newton on k with the Hellmann-Feynman slope (Eq. hellmann-feynman) and shifted
+//     inverse iteration for c converge to |lambda| = 1 exactly.
+//  3. Traveling modes are normalised to c^H M(lambda) c = L/2pi (Eq. normalization).
+//  4. Out-flow modes form the Bloch matrices B_d (|lambda| < 1 or dE/dk > 0) and
+//     B_s (|lambda_d| > 1 or dE/dk < 0, lambda_s = 1/lambda_d); Sigma = K' B Lambda B^-1
+//     with K'_d = K+, K'_s = K-; injection vectors B_gamma = (K' lambda_gamma - Sigma) c_gamma.
+#include <algorithm>
+#include <cmath>
+
+#include "pwqt_internal.cuh"
+
+namespace pwqt {
+
+size_t LeadEntry::bytes() const {
+    return sigma_d.bytes + sigma_s.bytes + P_d.bytes + P_s.bytes + v_out_d.bytes + v_out_s.bytes + rhs_d.bytes +
+           rhs_s.bytes + cin_s.bytes + v_in_d.bytes + v_in_s.bytes + sigma_d32.bytes + sigma_s32.bytes + rhs_d32.bytes +
+           rhs_s32.bytes;
+}
+
+// K0 = H0 - Ec M0, Kp = H1 - Ec M1, written column-major (inputs row-major).
+__global__ void k_lead_K(int n, double Ec, const double2* H0, const double2* H1, const double2* M0, const double2* M1,
+                         double2* K0cm, double2* Kpcm) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+    if (c >= n) return;
+    size_t rm = (size_t)r * n + c, cm = (size_t)c * n + r;
+    K0cm[cm] = csub(H0[rm], cscale(M0[rm], Ec));
+    Kpcm[cm] = csub(H1[rm], cscale(M1[rm], Ec));
+}
+
+// A + B and A - B of the symmetric pencil, column-major 2n x 2n.
+__global__ void k_lead_cayley(int n, const double2* K0, const double2* Kp, double2* ApB, double2* AmB) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x, c = blockIdx.y;   // r, c in [0, 2n)
+    int n2 = 2 * n;
+    if (r >= n2) return;
+    int br = r >= n, bc = c >= n, rr = r - br * n, cc = c - bc * n;
+    double2 k0 = K0[(size_t)cc * n + rr];
+    double2 kp = Kp[(size_t)cc * n + rr];
+    double2 km = cconj(Kp[(size_t)rr * n + cc]);   // K- = K+^H
+    double2 a, b;
+    if (!br && !bc) { a = k0; b = cscale(kp, -1.0); }
+    else if (!br && bc) { a = km; b = make_double2(0, 0); }
+    else if (br && !bc) { a = kp; b = make_double2(0, 0); }
+    else { a = make_double2(0, 0); b = kp; }
+    ApB[(size_t)c * n2 + r] = cadd(a, b);
+    AmB[(size_t)c * n2 + r] = csub(a, b);
+}
+
+// lambda_j from mu_j, unit-norm mode vectors c_j = lower half of the eigenvectors.
+__global__ void k_lead_modes(int n, const double2* __restrict__ mu, const double2* __restrict__ VR, double2* lam, double2* Cm) {
+    int j = blockIdx.x;
+    int n2 = 2 * n;
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) s += cnorm2(VR[(size_t)j * n2 + n + r]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    double inv = red[0] > 0 ? 1.0 / sqrt(red[0]) : 0.0;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) Cm[(size_t)j * n + r] = cscale(VR[(size_t)j * n2 + n + r], inv);
+    if (threadIdx.x == 0) {
+        // C = (A + B)^-1 (A - B): (A - B) x = mu (A + B) x  =>  A x = (1 + mu)/(1 - mu) B x
+        double2 m = mu[j];
+        lam[j] = cdiv(make_double2(1.0 + m.x, m.y), make_double2(1.0 - m.x, -m.y));
+    }
+}
+
+// Q = H(k) - Ec M(k) and M(k), column-major, H(k) = H0 + H1 ph + H1^H / ph.
+__global__ void k_lead_hk(int n, double2 ph, double Ec, const double2* H0, const double2* H1, const double2* M0,
+                          const double2* M1, double2* Qcm, double2* Mkcm) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+    if (c >= n) return;
+    size_t rm = (size_t)r * n + c, tm = (size_t)c * n + r;
+    double2 iph = cconj(ph);   // |ph| = 1
+    double2 hk = cadd(H0[rm], cadd(cmul(H1[rm], ph), cmul(cconj(H1[tm]), iph)));
+    double2 mk = cadd(M0[rm], cadd(cmul(M1[rm], ph), cmul(cconj(M1[tm]), iph)));
+    Qcm[(size_t)c * n + r] = csub(hk, cscale(mk, Ec));
+    Mkcm[(size_t)c * n + r] = mk;
+}
+
+// y = Mk x (Mk column-major)
+__global__ void k_matvec_cm(int n, const double2* __restrict__ A, const double2* __restrict__ x, double2* y) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double2 s = make_double2(0, 0);
+    for (int k = 0; k < n; ++k) cfma(s, A[(size_t)k * n + r], x[k]);
+    y[r] = s;
+}
+
+// One block: normalise x, and evaluate the forms needed for the Newton step at energy w:
+// out[0] = x^H H(k) x / x^H M(k) x (Rayleigh quotient w), out[1] = x^H M(k) x,
+// out[2] = x^H [iL(ph K+(w) - K+(w)^H / ph)] x / x^H M(k) x  (dE/dk of that band at k).
+__global__ void k_lead_forms(int n, double2 ph, double L, const double2* H0, const double2* H1, const double2* M0,
+                             const double2* M1, double2* x, double* out) {
+    __shared__ double red[3][256];
+    __shared__ double scale;
+    double s = 0.0;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) s += cnorm2(x[r]);
+    red[0][threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[0][threadIdx.x] += red[0][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) scale = 1.0 / sqrt(red[0][0]);
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x) x[r] = cscale(x[r], scale);
+    __syncthreads();
+    double2 iph = cconj(ph);
+    // per row r: (H(k) x)_r, (M(k) x)_r, (H1 x)_r ph - (H1^H x)_r / ph, same with M1
+    double hq = 0, mq = 0, dh = 0, dm = 0;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        double2 h0 = {0, 0}, h1 = {0, 0}, h1h = {0, 0}, m0 = {0, 0}, m1 = {0, 0}, m1h = {0, 0};
+        for (int k = 0; k < n; ++k) {
+            double2 xk = x[k];
+            cfma(h0, H0[(size_t)r * n + k], xk);
+            cfma(h1, H1[(size_t)r * n + k], xk);
+            cfma_cj(h1h, H1[(size_t)k * n + r], xk);
+            cfma(m0, M0[(size_t)r * n + k], xk);
+            cfma(m1, M1[(size_t)r * n + k], xk);
+            cfma_cj(m1h, M1[(size_t)k * n + r], xk);
+        }
+        double2 hx = cadd(h0, cadd(cmul(h1, ph), cmul(h1h, iph)));
+        double2 mx = cadd(m0, cadd(cmul(m1, ph), cmul(m1h, iph)));
+        double2 dhx = csub(cmul(h1, ph), cmul(h1h, iph));
+        double2 dmx = csub(cmul(m1, ph), cmul(m1h, iph));
+        double2 xr = cconj(x[r]);
+        hq += cmul(xr, hx).x;
+        mq += cmul(xr, mx).x;
+        // x^H (i L D) x = -L Im(x^H D x)... computed as real part of i L x^H D x
+        double2 t = cmul(xr, dhx);
+        dh += -L * t.y;
+        t = cmul(xr, dmx);
+        dm += -L * t.y;
+    }
+    red[0][threadIdx.x] = hq;
+    red[1][threadIdx.x] = mq;
+    red[2][threadIdx.x] = 0;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) { red[0][threadIdx.x] += red[0][threadIdx.x + w]; red[1][threadIdx.x] += red[1][threadIdx.x + w]; }
+        __syncthreads();
+    }
+    double H = red[0][0], M = red[1][0];
+    __syncthreads();
+    red[0][threadIdx.x] = dh;
+    red[1][threadIdx.x] = dm;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) { red[0][threadIdx.x] += red[0][threadIdx.x + w]; red[1][threadIdx.x] += red[1][threadIdx.x + w]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double wq = H / M;
+        out[0] = wq;
+        out[1] = M;
+        out[2] = (red[0][0] - wq * red[1][0]) / M;
+    }
+}
+
+// gather columns idx[j] of Cm (n x 2n col-major) scaled by s[j] into out (n x m col-major)
+__global__ void k_gather_cols(int n, const double2* __restrict__ Cm, const int* __restrict__ idx, const double2* __restrict__ s,
+                              double2* out) {
+    int j = blockIdx.y, r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    out[(size_t)j * n + r] = s ? cmul(Cm[(size_t)idx[j] * n + r], s[j]) : Cm[(size_t)idx[j] * n + r];
+}
+__global__ void k_identity(int n, double2* I) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x, c = blockIdx.y;
+    if (r < n) I[(size_t)c * n + r] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+}
+// rows idx[q] of the col-major n x n matrix A -> row-major out (m x n)
+__global__ void k_gather_rows(int n, const double2* __restrict__ A, const int* __restrict__ rows, double2* out) {
+    int q = blockIdx.y, c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n) out[(size_t)q * n + c] = A[(size_t)c * n + rows[q]];
+}
+__global__ void k_scale_col(double2* C, int n, int j, double s) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) C[(size_t)j * n + r] = cscale(C[(size_t)j * n + r], s);
+}
+__global__ void k_copy_col(double2* dst, const double2* src, int n) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) dst[r] = src[r];
+}
+
+namespace {
+struct LinSolve {
+    DBuf ipiv, info, work;
+    std::vector<char> hwork;
+};
+
+int lu_solve(pwqt_ctx* c, LinSolve& ls, int n, double2* A, double2* B, int nrhs) {
+    size_t wd = 0, wh = 0;
+    PWQT_SOLVER(c, cusolverDnXgetrf_bufferSize(c->sol, c->prm, n, n, CUDA_C_64F, A, n, CUDA_C_64F, &wd, &wh));
+    if (ls.work.bytes < wd) PWQT_TRY(alloc(c, ls.work, wd));
+    if (ls.ipiv.bytes < sizeof(int64_t) * n) PWQT_TRY(alloc(c, ls.ipiv, sizeof(int64_t) * n));
+    if (!ls.info.p) PWQT_TRY(alloc(c, ls.info, sizeof(int)));
+    if (ls.hwork.size() < wh + 16) ls.hwork.resize(wh + 16);
+    PWQT_SOLVER(c, cusolverDnXgetrf(c->sol, c->prm, n, n, CUDA_C_64F, A, n, ls.ipiv.as<int64_t>(), CUDA_C_64F, ls.work.p,
+                                    wd, ls.hwork.data(), wh, ls.info.as<int>()));
+    PWQT_SOLVER(c, cusolverDnXgetrs(c->sol, c->prm, CUBLAS_OP_N, n, nrhs, CUDA_C_64F, A, n, ls.ipiv.as<int64_t>(),
+                                    CUDA_C_64F, B, n, ls.info.as<int>()));
+    return PWQT_OK;
+}
+}  // namespace
+
+int lead_entry(pwqt_ctx* c, double Ec, LeadEntry** out) {
+    auto it = c->cache.find(Ec);
+    if (it != c->cache.end()) { *out = it->second.get(); return PWQT_OK; }
+    const int n = c->n, n2 = 2 * n;
+    const double L = c->Lz;
+    cudaStream_t st = c->stream;
+    const dim3 b128(128);
+    DBuf K0, Kp, ApB, AmB, Wmu, VR, lam, Cm, Q, Mk, x, y, forms;
+    PWQT_TRY(alloc(c, K0, sizeof(double2) * n * n));
+    PWQT_TRY(alloc(c, Kp, sizeof(double2) * n * n));
+    PWQT_TRY(alloc(c, ApB, sizeof(double2) * (size_t)n2 * n2));
+    PWQT_TRY(alloc(c, AmB, sizeof(double2) * (size_t)n2 * n2));
+    k_lead_K<<<dim3((n + 127) / 128, n), b128, 0, st>>>(n, Ec, c->H0.as<double2>(), c->H1.as<double2>(), c->M0.as<double2>(),
+                                                      c->M1.as<double2>(), K0.as<double2>(), Kp.as<double2>());
+    k_lead_cayley<<<dim3((n2 + 127) / 128, n2), b128, 0, st>>>(n, K0.as<double2>(), Kp.as<double2>(), ApB.as<double2>(),
+                                                             AmB.as<double2>());
+    c->launches += 2;
+    PWQT_CUDA(c, cudaGetLastError());
+    LinSolve ls;
+    PWQT_TRY(lu_solve(c, ls, n2, ApB.as<double2>(), AmB.as<double2>(), n2));   // AmB <- (A+B)^-1 (A-B)
+    // eigen-decomposition of the Cayley-transformed pencil
+    PWQT_TRY(alloc(c, Wmu, sizeof(double2) * n2));
+    PWQT_TRY(alloc(c, VR, sizeof(double2) * (size_t)n2 * n2));
+    size_t wd = 0, wh = 0;
+    PWQT_SOLVER(c, cusolverDnXgeev_bufferSize(c->sol, c->prm, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR, n2, CUDA_C_64F,
+                                              AmB.p, n2, CUDA_C_64F, Wmu.p, CUDA_C_64F, nullptr, n2, CUDA_C_64F, VR.p, n2,
+                                              CUDA_C_64F, &wd, &wh));
+    DBuf gw;
+    PWQT_TRY(alloc(c, gw, std::max<size_t>(wd, 16)));
+    std::vector<char> gh(wh + 16);
+    PWQT_SOLVER(c, cusolverDnXgeev(c->sol, c->prm, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR, n2, CUDA_C_64F, AmB.p, n2,
+                                   CUDA_C_64F, Wmu.p, CUDA_C_64F, nullptr, n2, CUDA_C_64F, VR.p, n2, CUDA_C_64F, gw.p, wd,
+                                   gh.data(), wh, ls.info.as<int>()));
+    int hinfo = 0;
+    PWQT_CUDA(c, cudaMemcpyAsync(&hinfo, ls.info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ApB.release(); gw.release();
+    PWQT_TRY(alloc(c, lam, sizeof(double2) * n2));
+    PWQT_TRY(alloc(c, Cm, sizeof(double2) * (size_t)n * n2));
+    k_lead_modes<<<n2, 256, 0, st>>>(n, Wmu.as<double2>(), VR.as<double2>(), lam.as<double2>(), Cm.as<double2>());
+    c->launches++;
+    PWQT_CUDA(c, cudaGetLastError());
+    std::vector<double2> hlam(n2);
+    PWQT_CUDA(c, cudaMemcpyAsync(hlam.data(), lam.p, sizeof(double2) * n2, cudaMemcpyDeviceToHost, st));
+    PWQT_CUDA(c, cudaStreamSynchronize(st));
+    if (hinfo != 0) return fail(c, PWQT_ERR_CUDA, "non-Hermitian eigensolver info " + std::to_string(hinfo));
+    VR.release(); AmB.release(); Wmu.release();
+
+    // ---- traveling modes: refine onto the unit circle
+    std::vector<char> trav(n2, 0);
+    std::vector<double> dEdk(n2, 0.0);
+    int status = 0;
+    PWQT_TRY(alloc(c, Q, sizeof(double2) * n * n));
+    PWQT_TRY(alloc(c, Mk, sizeof(double2) * n * n));
+    PWQT_TRY(alloc(c, x, sizeof(double2) * n));
+    PWQT_TRY(alloc(c, y, sizeof(double2) * n));
+    PWQT_TRY(alloc(c, forms, sizeof(double) * 4));
+    const double tol_E = 1e-13 * std::max(1.0, std::fabs(Ec));
+    for (int j = 0; j < n2; ++j) {
+        double al = std::hypot(hlam[j].x, hlam[j].y);
+        if (std::fabs(al - 1.0) >= 1e-6) {
+            if (std::fabs(al - 1.0) < 1e-5) status |= PWQT_ST_NEAR_UNIT;
+            continue;
+        }
+        trav[j] = 1;
+        double k = std::atan2(hlam[j].y, hlam[j].x) / L;
+        PWQT_CUDA(c, cudaMemcpyAsync(x.p, Cm.as<double2>() + (size_t)j * n, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+        double hf[4] = {0, 0, 0, 0};
+        double2 ph = make_double2(std::cos(k * L), std::sin(k * L));
+        for (int iter = 0; iter < 8; ++iter) {
+            ph = make_double2(std::cos(k * L), std::sin(k * L));
+            k_lead_hk<<<dim3((n + 127) / 128, n), b128, 0, st>>>(n, ph, Ec, c->H0.as<double2>(), c->H1.as<double2>(),
+                                                               c->M0.as<double2>(), c->M1.as<double2>(), Q.as<double2>(),
+                                                               Mk.as<double2>());
+            k_matvec_cm<<<(n + 127) / 128, b128, 0, st>>>(n, Mk.as<double2>(), x.as<double2>(), y.as<double2>());
+            c->launches += 2;
+            PWQT_TRY(lu_solve(c, ls, n, Q.as<double2>(), y.as<double2>(), 1));   // y <- (H(k) - Ec M(k))^-1 M(k) x
+            PWQT_CUDA(c, cudaMemcpyAsync(x.p, y.p, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+            k_lead_forms<<<1, 256, 0, st>>>(n, ph, L, c->H0.as<double2>(), c->H1.as<double2>(), c->M0.as<double2>(),
+                                            c->M1.as<double2>(), x.as<double2>(), forms.as<double>());
+            c->launches++;
+            PWQT_CUDA(c, cudaMemcpyAsync(hf, forms.p, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
+            PWQT_CUDA(c, cudaStreamSynchronize(st));
+            double w = hf[0], slope = hf[2];
+            if (std::fabs(w - Ec) < tol_E || slope == 0.0 || !std::isfinite(slope)) break;
+            k -= (w - Ec) / slope;
+        }
+        hlam[j] = ph;
+        dEdk[j] = hf[2];
+        // normalise to c^H M(lambda) c = L / 2pi and store back
+        double scale = std::sqrt(L / (2.0 * M_PI) / hf[1]);
+        PWQT_CUDA(c, cudaMemcpyAsync(Cm.as<double2>() + (size_t)j * n, x.p, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+        k_scale_col<<<(n + 127) / 128, b128, 0, st>>>(Cm.as<double2>(), n, j, scale);
+        c->launches++;
+    }
+    // degenerate traveling modes (same lambda) are not flux-orthogonalised here: flag them
+    for (int a = 0; a < n2; ++a)
+        for (int b = a + 1; b < n2; ++b)
+            if (trav[a] && trav[b] && std::hypot(hlam[a].x - hlam[b].x, hlam[a].y - hlam[b].y) < 1e-8) status |= PWQT_ST_DEGENERATE;
+
+    // ---- classification (drain convention lambda = c_{i+1}/c_i)
+    std::vector<int> out_d, in_d, out_s, in_s;
+    for (int j = 0; j < n2; ++j) {
+        double al = std::hypot(hlam[j].x, hlam[j].y);
+        if (trav[j]) {
+            if (dEdk[j] > 0) { out_d.push_back(j); in_s.push_back(j); }
+            else { out_s.push_back(j); in_d.push_back(j); }
+        } else if (al < 1.0) out_d.push_back(j);
+        else out_s.push_back(j);
+    }
+    auto E = std::make_unique<LeadEntry>();
+    E->Ec = Ec;
+    if ((int)out_d.size() != n || (int)out_s.size() != n) {
+        E->status = status | PWQT_ST_MODE_COUNT;
+        c->cache[Ec] = std::move(E);
+        *out = c->cache[Ec].get();
+        return PWQT_OK;
+    }
+    // ---- self-energies, projections and injection vectors for both contacts
+    auto build = [&](bool drain, DBuf& sigma, DBuf& P, DBuf& vout, DBuf& rhs, DBuf& vin, DBuf* cin, int& ntrav,
+                     int& min) -> int {
+        const std::vector<int>& outl = drain ? out_d : out_s;
+        const std::vector<int>& inl = drain ? in_d : in_s;
+        std::vector<double2> lo(n), li(inl.size());
+        std::vector<int> trows;
+        std::vector<double> tv;
+        for (int q = 0; q < n; ++q) {
+            double2 l = hlam[outl[q]];
+            if (!drain) { double a2 = l.x * l.x + l.y * l.y; l = make_double2(l.x / a2, -l.y / a2); }
+            lo[q] = l;
+            if (trav[outl[q]]) { trows.push_back(q); tv.push_back(std::fabs(dEdk[outl[q]])); }
+        }
+        for (size_t q = 0; q < inl.size(); ++q) {
+            double2 l = hlam[inl[q]];
+            if (!drain) { double a2 = l.x * l.x + l.y * l.y; l = make_double2(l.x / a2, -l.y / a2); }
+            li[q] = l;
+        }
+        ntrav = (int)trows.size();
+        min = (int)inl.size();
+        DBuf didx, dlam, B, BL, Binv, T1, S, Cin, dli, dtr, R1;
+        PWQT_TRY(alloc(c, didx, sizeof(int) * n));
+        PWQT_TRY(alloc(c, dlam, sizeof(double2) * n));
+        PWQT_CUDA(c, cudaMemcpyAsync(didx.p, outl.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+        PWQT_CUDA(c, cudaMemcpyAsync(dlam.p, lo.data(), sizeof(double2) * n, cudaMemcpyHostToDevice, st));
+        PWQT_TRY(alloc(c, B, sizeof(double2) * n * n));
+        PWQT_TRY(alloc(c, BL, sizeof(double2) * n * n));
+        PWQT_TRY(alloc(c, Binv, sizeof(double2) * n * n));
+        PWQT_TRY(alloc(c, T1, sizeof(double2) * n * n));
+        PWQT_TRY(alloc(c, S, sizeof(double2) * n * n));
+        k_gather_cols<<<dim3((n + 127) / 128, n), b128, 0, st>>>(n, Cm.as<double2>(), didx.as<int>(), nullptr, B.as<double2>());
+        k_gather_cols<<<dim3((n + 127) / 128, n), b128, 0, st>>>(n, Cm.as<double2>(), didx.as<int>(), dlam.as<double2>(), BL.as<double2>());
+        k_identity<<<dim3((n + 127) / 128, n), b128, 0, st>>>(n, Binv.as<double2>());
+        c->launches += 3;
+        PWQT_TRY(lu_solve(c, ls, n, B.as<double2>(), Binv.as<double2>(), n));   // Binv = B^-1
+        cuDoubleComplex one = {1, 0}, zero = {0, 0}, mone = {-1, 0};
+        // T1 = (B Lambda) B^-1 ; Sigma = K' T1   (K'_d = K+, K'_s = K- = K+^H), column-major
+        PWQT_BLAS(c, cublasZgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, BL.as<cuDoubleComplex>(), n,
+                                 Binv.as<cuDoubleComplex>(), n, &zero, T1.as<cuDoubleComplex>(), n));
+        PWQT_BLAS(c, cublasZgemm(c->blas, drain ? CUBLAS_OP_N : CUBLAS_OP_C, CUBLAS_OP_N, n, n, n, &one, Kp.as<cuDoubleComplex>(), n,
+                                 T1.as<cuDoubleComplex>(), n, &zero, S.as<cuDoubleComplex>(), n));
+        PWQT_TRY(alloc(c, sigma, sizeof(double2) * n * n));
+        transpose_c128(S.as<double2>(), sigma.as<double2>(), n, n, st);   // column-major -> row-major
+        c->launches++;
+        // rows of B^-1 for traveling out-flow modes
+        PWQT_TRY(alloc(c, P, sizeof(double2) * (size_t)std::max(ntrav, 1) * n));
+        PWQT_TRY(alloc(c, vout, sizeof(double) * std::max(ntrav, 1)));
+        if (ntrav) {
+            PWQT_TRY(alloc(c, dtr, sizeof(int) * ntrav));
+            PWQT_CUDA(c, cudaMemcpyAsync(dtr.p, trows.data(), sizeof(int) * ntrav, cudaMemcpyHostToDevice, st));
+            k_gather_rows<<<dim3((n + 127) / 128, ntrav), b128, 0, st>>>(n, Binv.as<double2>(), dtr.as<int>(), P.as<double2>());
+            c->launches++;
+            PWQT_CUDA(c, cudaMemcpyAsync(vout.p, tv.data(), sizeof(double) * ntrav, cudaMemcpyHostToDevice, st));
+        }
+        // injection vectors rhs = K' C_in Lambda_in - Sigma C_in  (n x m), stored row-major
+        int m = min;
+        PWQT_TRY(alloc(c, rhs, sizeof(double2) * (size_t)n * std::max(m, 1)));
+        PWQT_TRY(alloc(c, vin, sizeof(double) * std::max(m, 1)));
+        if (cin) PWQT_TRY(alloc(c, *cin, sizeof(double2) * (size_t)n * std::max(m, 1)));
+        if (m) {
+            std::vector<double> hv(m);
+            for (int q = 0; q < m; ++q) hv[q] = std::fabs(dEdk[inl[q]]);
+            PWQT_CUDA(c, cudaMemcpyAsync(vin.p, hv.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
+            PWQT_TRY(alloc(c, Cin, sizeof(double2) * (size_t)n * m));
+            PWQT_TRY(alloc(c, R1, sizeof(double2) * (size_t)n * m));
+            PWQT_TRY(alloc(c, dli, sizeof(double2) * m));
+            DBuf didx2;
+            PWQT_TRY(alloc(c, didx2, sizeof(int) * m));
+            PWQT_CUDA(c, cudaMemcpyAsync(didx2.p, inl.data(), sizeof(int) * m, cudaMemcpyHostToDevice, st));
+            PWQT_CUDA(c, cudaMemcpyAsync(dli.p, li.data(), sizeof(double2) * m, cudaMemcpyHostToDevice, st));
+            DBuf CinL;
+            PWQT_TRY(alloc(c, CinL, sizeof(double2) * (size_t)n * m));
+            k_gather_cols<<<dim3((n + 127) / 128, m), b128, 0, st>>>(n, Cm.as<double2>(), didx2.as<int>(), nullptr, Cin.as<double2>());
+            k_gather_cols<<<dim3((n + 127) / 128, m), b128, 0, st>>>(n, Cm.as<double2>(), didx2.as<int>(), dli.as<double2>(), CinL.as<double2>());
+            c->launches += 2;
+            // R1 = K' (C_in Lambda) - Sigma C_in
+            PWQT_BLAS(c, cublasZgemm(c->blas, drain ? CUBLAS_OP_N : CUBLAS_OP_C, CUBLAS_OP_N, n, m, n, &one,
+                                     Kp.as<cuDoubleComplex>(), n, CinL.as<cuDoubleComplex>(), n, &zero, R1.as<cuDoubleComplex>(), n));
+            PWQT_BLAS(c, cublasZgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, m, n, &mone, S.as<cuDoubleComplex>(), n,
+                                     Cin.as<cuDoubleComplex>(), n, &one, R1.as<cuDoubleComplex>(), n));
+            transpose_c128(R1.as<double2>(), rhs.as<double2>(), m, n, st);   // (n x m col-major) -> row-major n x m
+            if (cin) transpose_c128(Cin.as<double2>(), cin->as<double2>(), m, n, st);
+            c->launches += 2;
+        }
+        PWQT_CUDA(c, cudaStreamSynchronize(st));
+        return PWQT_OK;
+    };
+    PWQT_BLAS(c, cublasSetStream(c->blas, st));
+    PWQT_TRY(build(true, E->sigma_d, E->P_d, E->v_out_d, E->rhs_d, E->v_in_d, nullptr, E->n_trav_out_d, E->m_in_d));
+    PWQT_TRY(build(false, E->sigma_s, E->P_s, E->v_out_s, E->rhs_s, E->v_in_s, &E->cin_s, E->n_trav_out_s, E->m_in_s));
+    size_t nn = (size_t)n * n;
+    PWQT_TRY(alloc(c, E->sigma_d32, sizeof(float2) * nn));
+    PWQT_TRY(alloc(c, E->sigma_s32, sizeof(float2) * nn));
+    PWQT_TRY(alloc(c, E->rhs_d32, sizeof(float2) * (size_t)n * std::max(E->m_in_d, 1)));
+    PWQT_TRY(alloc(c, E->rhs_s32, sizeof(float2) * (size_t)n * std::max(E->m_in_s, 1)));
+    c128_to_c64(E->sigma_d.as<double2>(), E->sigma_d32.as<float2>(), nn, st);
+    c128_to_c64(E->sigma_s.as<double2>(), E->sigma_s32.as<float2>(), nn, st);
+    c128_to_c64(E->rhs_d.as<double2>(), E->rhs_d32.as<float2>(), (size_t)n * E->m_in_d, st);
+    c128_to_c64(E->rhs_s.as<double2>(), E->rhs_s32.as<float2>(), (size_t)n * E->m_in_s, st);
+    c->launches += 4;
+    PWQT_CUDA(c, cudaStreamSynchronize(st));
+    E->status = status;
+    c->cache[Ec] = std::move(E);
+    *out = c->cache[Ec].get();
+    return PWQT_OK;
+}
+
+}  // namespace pwqt

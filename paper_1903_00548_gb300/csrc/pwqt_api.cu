@@ -1,0 +1,255 @@
+// extern "C" entry points of libpwqt (declared and documented in include/pwqt.h).
+#include <cmath>
+#include <cstring>
+
+#include "pwqt_internal.cuh"
+
+using namespace pwqt;
+
+namespace {
+int check_ctx(pwqt_ctx* c) { return c ? PWQT_OK : PWQT_ERR_INVALID_ARG; }
+
+// H(k') and M(k') (column-major) for the band reconstruction of Sec. 5.1.
+__global__ void k_bands_hk(int n, double2 ph, const double2* H0, const double2* H1, const double2* M0, const double2* M1,
+                           double2* Hk, double2* Mk) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+    if (c >= n) return;
+    size_t rm = (size_t)r * n + c, tm = (size_t)c * n + r;
+    double2 iph = cconj(ph);
+    Hk[(size_t)c * n + r] = cadd(H0[rm], cadd(cmul(H1[rm], ph), cmul(cconj(H1[tm]), iph)));
+    Mk[(size_t)c * n + r] = cadd(M0[rm], cadd(cmul(M1[rm], ph), cmul(cconj(M1[tm]), iph)));
+}
+
+int solve_common(pwqt_ctx* c, int sys, int n_E, const double* E, int precision, SolveOut& dev, cudaStream_t st) {
+    if (!c->n) return fail(c, PWQT_ERR_STATE, "no basis: call pwqt_assemble_intrinsic first");
+    auto it = c->systems.find(sys);
+    if (it == c->systems.end()) return fail(c, PWQT_ERR_STATE, "unknown system: call pwqt_set_extrinsic first");
+    if (precision != PWQT_FP64 && precision != PWQT_MIXED) return fail(c, PWQT_ERR_INVALID_ARG, "bad precision");
+    if (n_E < 0 || (n_E > 0 && !E)) return fail(c, PWQT_ERR_INVALID_ARG, "bad energies");
+    if (c->n > 1024) return fail(c, PWQT_ERR_INVALID_ARG, "block size above 1024");
+    for (int e = 0; e < n_E; ++e)
+        if (!std::isfinite(E[e])) return fail(c, PWQT_ERR_INVALID_ARG, "non-finite energy");
+    return solve_batch(c, it->second, n_E, E, precision, dev, st);
+}
+}  // namespace
+
+extern "C" {
+
+int pwqt_create(pwqt_ctx** out, const pwqt_opts* opts) {
+    if (!out) return PWQT_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) { cudaGetLastError(); return PWQT_ERR_NO_DEVICE; }
+    auto* c = new pwqt_ctx();
+    if (opts) c->opts = *opts;
+    if (c->opts.ir_tol <= 0) c->opts.ir_tol = 1e-12;
+    if (c->opts.ir_max_iters <= 0) c->opts.ir_max_iters = 40;
+    c->dev = c->opts.device;
+    if (c->dev < 0 || c->dev >= ndev) { delete c; return PWQT_ERR_INVALID_ARG; }
+    if (cudaSetDevice(c->dev) != cudaSuccess) { delete c; return PWQT_ERR_CUDA; }
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev);
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cublasCreate(&c->blas) != CUBLAS_STATUS_SUCCESS || cusolverDnCreate(&c->sol) != CUSOLVER_STATUS_SUCCESS ||
+        cusolverDnCreateParams(&c->prm) != CUSOLVER_STATUS_SUCCESS) {
+        pwqt_destroy(c);
+        return PWQT_ERR_CUDA;
+    }
+    cublasSetStream(c->blas, c->stream);
+    cusolverDnSetStream(c->sol, c->stream);
+    *out = c;
+    return PWQT_OK;
+}
+
+int pwqt_destroy(pwqt_ctx* c) {
+    if (!c) return PWQT_OK;
+    cudaSetDevice(c->dev);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    c->cache.clear();
+    c->systems.clear();
+    if (c->prm) cusolverDnDestroyParams(c->prm);
+    if (c->sol) cusolverDnDestroy(c->sol);
+    if (c->blas) cublasDestroy(c->blas);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return PWQT_OK;
+}
+
+const char* pwqt_last_error(const pwqt_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int pwqt_assemble_intrinsic(pwqt_ctx* c, const pwqt_cell* cell, const pwqt_formfactor* ff, double gcut, int n_bands,
+                            int* n_out) {
+    PWQT_TRY(check_ctx(c));
+    if (!cell || !ff || !cell->atoms || cell->n_atoms <= 0 || n_bands <= 0 || gcut <= 0 || cell->Lz <= 0 || cell->Lx <= 0 ||
+        (cell->dim != 1 && cell->dim != 2))
+        return fail(c, PWQT_ERR_INVALID_ARG, "invalid cell / form factor / cutoff");
+    if (2 * n_bands > 1024) return fail(c, PWQT_ERR_INVALID_ARG, "block size 2*n_bands above 1024");
+    cudaSetDevice(c->dev);
+    PWQT_TRY(epm_basis(c, cell, ff, gcut, n_bands));
+    if (n_out) *n_out = c->n;
+    return PWQT_OK;
+}
+
+int pwqt_set_enhancement(pwqt_ctx* c, const pwqt_cell* cell, int n_bands, const double* eps, const int* n_pw,
+                         const int* mx, const int* mz, const double* coef, int* n_out) {
+    PWQT_TRY(check_ctx(c));
+    if (!cell || !eps || !n_pw || !mx || !mz || !coef || n_bands <= 0 || n_pw[0] < n_bands || n_pw[1] < n_bands ||
+        2 * n_bands > 1024 || cell->Lz <= 0 || cell->Lx <= 0)
+        return fail(c, PWQT_ERR_INVALID_ARG, "invalid enhancement-function input");
+    cudaSetDevice(c->dev);
+    size_t rows = (size_t)n_pw[0] + n_pw[1];
+    DBuf d;
+    PWQT_TRY(alloc(c, d, sizeof(double2) * rows * n_bands));
+    PWQT_CUDA(c, cudaMemcpy(d.p, coef, sizeof(double2) * rows * n_bands, cudaMemcpyHostToDevice));
+    PWQT_TRY(assemble_from_basis(c, cell, n_bands, eps, n_pw, mx, mz, d.as<double2>()));
+    if (n_out) *n_out = c->n;
+    return PWQT_OK;
+}
+
+int pwqt_get_blocks(pwqt_ctx* c, double* H0, double* H1, double* M0, double* M1, double* W) {
+    PWQT_TRY(check_ctx(c));
+    if (!c->n) return fail(c, PWQT_ERR_STATE, "no basis");
+    size_t nn = (size_t)c->n * c->n * sizeof(double2);
+    if (H0) PWQT_CUDA(c, cudaMemcpy(H0, c->H0.p, nn, cudaMemcpyDeviceToHost));
+    if (H1) PWQT_CUDA(c, cudaMemcpy(H1, c->H1.p, nn, cudaMemcpyDeviceToHost));
+    if (M0) PWQT_CUDA(c, cudaMemcpy(M0, c->M0.p, nn, cudaMemcpyDeviceToHost));
+    if (M1) PWQT_CUDA(c, cudaMemcpy(M1, c->M1.p, nn, cudaMemcpyDeviceToHost));
+    if (W) PWQT_CUDA(c, cudaMemcpy(W, c->W.p, 6 * nn, cudaMemcpyDeviceToHost));
+    return PWQT_OK;
+}
+
+int pwqt_set_extrinsic(pwqt_ctx* c, int sys, int n_nodes, const double* U) {
+    PWQT_TRY(check_ctx(c));
+    if (!c->n) return fail(c, PWQT_ERR_STATE, "no basis");
+    if (sys < 0 || sys >= 64 || n_nodes < 2 || !U) return fail(c, PWQT_ERR_INVALID_ARG, "invalid system / nodes / potential");
+    for (int i = 0; i < n_nodes; ++i)
+        if (!std::isfinite(U[i])) return fail(c, PWQT_ERR_INVALID_ARG, "non-finite potential");
+    cudaSetDevice(c->dev);
+    System& s = c->systems[sys];
+    s.N = n_nodes;
+    s.U.assign(U, U + n_nodes);
+    s.Us = U[0];
+    s.Ud = U[n_nodes - 1];
+    int r = build_system_blocks(c, s);
+    if (r != PWQT_OK) c->systems.erase(sys);
+    return r;
+}
+
+int pwqt_solve(pwqt_ctx* c, int sys, int n_E, const double* E, int precision, double* T, double* R, double* T_ds,
+               int* n_open, double* node_n, double* resid, int* iters, int* status) {
+    PWQT_TRY(check_ctx(c));
+    cudaSetDevice(c->dev);
+    auto it = c->systems.find(sys);
+    int N = it == c->systems.end() ? 0 : it->second.N;
+    if (n_E == 0) return PWQT_OK;
+    DBuf dE, dT, dR, dTds, dno, dnn, dres, dit, dst;
+    size_t ne = (size_t)std::max(n_E, 1);
+    PWQT_TRY(alloc(c, dT, sizeof(double) * ne));
+    PWQT_TRY(alloc(c, dR, sizeof(double) * ne));
+    PWQT_TRY(alloc(c, dTds, sizeof(double) * ne));
+    PWQT_TRY(alloc(c, dno, sizeof(int) * 2 * ne));
+    PWQT_TRY(alloc(c, dnn, sizeof(double) * 2 * ne * std::max(N, 1)));
+    PWQT_TRY(alloc(c, dres, sizeof(double) * ne));
+    PWQT_TRY(alloc(c, dit, sizeof(int) * ne));
+    PWQT_TRY(alloc(c, dst, sizeof(int) * ne));
+    SolveOut o{dT.as<double>(), dR.as<double>(), dTds.as<double>(), dnn.as<double>(), dres.as<double>(),
+               dno.as<int>(), dit.as<int>(), dst.as<int>()};
+    PWQT_TRY(solve_common(c, sys, n_E, E, precision, o, c->stream));
+    PWQT_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (T) PWQT_CUDA(c, cudaMemcpy(T, dT.p, sizeof(double) * n_E, cudaMemcpyDeviceToHost));
+    if (R) PWQT_CUDA(c, cudaMemcpy(R, dR.p, sizeof(double) * n_E, cudaMemcpyDeviceToHost));
+    if (T_ds) PWQT_CUDA(c, cudaMemcpy(T_ds, dTds.p, sizeof(double) * n_E, cudaMemcpyDeviceToHost));
+    if (n_open) PWQT_CUDA(c, cudaMemcpy(n_open, dno.p, sizeof(int) * 2 * n_E, cudaMemcpyDeviceToHost));
+    if (node_n) PWQT_CUDA(c, cudaMemcpy(node_n, dnn.p, sizeof(double) * 2 * n_E * N, cudaMemcpyDeviceToHost));
+    if (resid) PWQT_CUDA(c, cudaMemcpy(resid, dres.p, sizeof(double) * n_E, cudaMemcpyDeviceToHost));
+    if (iters) PWQT_CUDA(c, cudaMemcpy(iters, dit.p, sizeof(int) * n_E, cudaMemcpyDeviceToHost));
+    if (status) PWQT_CUDA(c, cudaMemcpy(status, dst.p, sizeof(int) * n_E, cudaMemcpyDeviceToHost));
+    return PWQT_OK;
+}
+
+int pwqt_solve_dev(pwqt_ctx* c, int sys, int n_E, const double* E, int precision, double* T, double* R, double* T_ds,
+                   int* n_open, double* node_n, double* resid, int* iters, int* status, void* stream) {
+    PWQT_TRY(check_ctx(c));
+    cudaSetDevice(c->dev);
+    auto it = c->systems.find(sys);
+    int N = it == c->systems.end() ? 0 : it->second.N;
+    if (n_E == 0) return PWQT_OK;
+    // outputs the caller did not ask for go to context scratch
+    size_t ne = (size_t)n_E;
+    size_t need = sizeof(double) * ne * (4 + 2 * std::max(N, 1)) + sizeof(int) * ne * 4 + 1024;
+    if (c->work_a.bytes < need) PWQT_TRY(alloc(c, c->work_a, need));
+    char* w = c->work_a.as<char>();
+    auto take = [&](size_t b) { char* p = w; w += (b + 255) / 256 * 256; return p; };
+    SolveOut o;
+    o.T = T ? T : (double*)take(sizeof(double) * ne);
+    o.R = R ? R : (double*)take(sizeof(double) * ne);
+    o.T_ds = T_ds ? T_ds : (double*)take(sizeof(double) * ne);
+    o.resid = resid ? resid : (double*)take(sizeof(double) * ne);
+    o.node_n = node_n ? node_n : (double*)take(sizeof(double) * ne * 2 * std::max(N, 1));
+    o.n_open = n_open ? n_open : (int*)take(sizeof(int) * ne * 2);
+    o.iters = iters ? iters : (int*)take(sizeof(int) * ne);
+    o.status = status ? status : (int*)take(sizeof(int) * ne);
+    cudaStream_t st = stream ? (cudaStream_t)stream : (cudaStream_t)0;
+    return solve_common(c, sys, n_E, E, precision, o, st);
+}
+
+int pwqt_prepare_leads(pwqt_ctx* c, int sys, int n_E, const double* E) {
+    PWQT_TRY(check_ctx(c));
+    auto it = c->systems.find(sys);
+    if (it == c->systems.end()) return fail(c, PWQT_ERR_STATE, "unknown system");
+    if (n_E < 0 || (n_E && !E)) return fail(c, PWQT_ERR_INVALID_ARG, "bad energies");
+    cudaSetDevice(c->dev);
+    for (int e = 0; e < n_E; ++e) {
+        LeadEntry* le;
+        PWQT_TRY(lead_entry(c, E[e] - it->second.Us, &le));
+        PWQT_TRY(lead_entry(c, E[e] - it->second.Ud, &le));
+    }
+    return PWQT_OK;
+}
+
+int pwqt_cache_info(pwqt_ctx* c, int* entries, size_t* bytes) {
+    PWQT_TRY(check_ctx(c));
+    size_t b = 0;
+    for (auto& kv : c->cache) b += kv.second->bytes();
+    if (entries) *entries = (int)c->cache.size();
+    if (bytes) *bytes = b;
+    return PWQT_OK;
+}
+
+int pwqt_bands(pwqt_ctx* c, int n_k, const double* k, double* E_out) {
+    PWQT_TRY(check_ctx(c));
+    if (!c->n) return fail(c, PWQT_ERR_STATE, "no basis");
+    if (n_k < 0 || (n_k && (!k || !E_out))) return fail(c, PWQT_ERR_INVALID_ARG, "bad k list");
+    cudaSetDevice(c->dev);
+    int n = c->n;
+    DBuf Hk, Mk, W, info, work;
+    PWQT_TRY(alloc(c, Hk, sizeof(double2) * n * n));
+    PWQT_TRY(alloc(c, Mk, sizeof(double2) * n * n));
+    PWQT_TRY(alloc(c, W, sizeof(double) * n));
+    PWQT_TRY(alloc(c, info, sizeof(int)));
+    int lwork = 0;
+    PWQT_SOLVER(c, cusolverDnZhegvd_bufferSize(c->sol, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n,
+                                               Hk.as<cuDoubleComplex>(), n, Mk.as<cuDoubleComplex>(), n, W.as<double>(), &lwork));
+    PWQT_TRY(alloc(c, work, sizeof(cuDoubleComplex) * std::max(lwork, 1)));
+    for (int q = 0; q < n_k; ++q) {
+        double2 ph = make_double2(std::cos(k[q] * c->Lz), std::sin(k[q] * c->Lz));
+        k_bands_hk<<<dim3((n + 127) / 128, n), 128, 0, c->stream>>>(n, ph, c->H0.as<double2>(), c->H1.as<double2>(),
+                                                                 c->M0.as<double2>(), c->M1.as<double2>(), Hk.as<double2>(),
+                                                                 Mk.as<double2>());
+        c->launches++;
+        PWQT_SOLVER(c, cusolverDnZhegvd(c->sol, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n,
+                                        Hk.as<cuDoubleComplex>(), n, Mk.as<cuDoubleComplex>(), n, W.as<double>(),
+                                        work.as<cuDoubleComplex>(), lwork, info.as<int>()));
+        PWQT_CUDA(c, cudaMemcpyAsync(E_out + (size_t)q * n, W.p, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    }
+    PWQT_CUDA(c, cudaStreamSynchronize(c->stream));
+    return PWQT_OK;
+}
+
+int pwqt_kernel_launches(pwqt_ctx* c, long long* count, int reset) {
+    PWQT_TRY(check_ctx(c));
+    if (count) *count = c->launches;
+    if (reset) c->launches = 0;
+    return PWQT_OK;
+}
+
+}  // extern "C"

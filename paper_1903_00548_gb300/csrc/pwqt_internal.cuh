@@ -1,0 +1,145 @@
+// Internal declarations shared by the libpwqt translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/pwqt.h"
+
+namespace pwqt {
+
+constexpr double HB2M = 0.0380998212;   // hbar^2 / 2 m_e  (eV nm^2)
+
+// ---------------------------------------------------------------- complex math
+struct cplx { double x, y; };
+__host__ __device__ inline double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__host__ __device__ inline double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ inline double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// a += b * c
+__host__ __device__ inline void cfma(double2& a, double2 b, double2 c) {
+    a.x = fma(b.x, c.x, fma(-b.y, c.y, a.x));
+    a.y = fma(b.x, c.y, fma(b.y, c.x, a.y));
+}
+// a += conj(b) * c
+__host__ __device__ inline void cfma_cj(double2& a, double2 b, double2 c) {
+    a.x = fma(b.x, c.x, fma(b.y, c.y, a.x));
+    a.y = fma(b.x, c.y, fma(-b.y, c.x, a.y));
+}
+__host__ __device__ inline double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
+__host__ __device__ inline double cnorm2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ inline double2 cdiv(double2 a, double2 b) {
+    // Smith's algorithm
+    if (fabs(b.x) >= fabs(b.y)) {
+        double r = b.y / b.x, d = b.x + b.y * r;
+        return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+    } else {
+        double r = b.x / b.y, d = b.x * r + b.y;
+        return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+    }
+}
+
+// ---------------------------------------------------------------- device buffer
+struct DBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DBuf& operator=(DBuf&& o) noexcept { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; return *this; }
+    ~DBuf() { release(); }
+    void release() { if (p) cudaFree(p); p = nullptr; bytes = 0; }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ---------------------------------------------------------------- cached contact data
+// One entry per lead energy Ec = E - U_lead: drain-side and source-side data of the
+// same complex band structure (lambda_s = 1/lambda_d with the same mode vectors).
+struct LeadEntry {
+    double Ec = 0;
+    int n_trav_out_d = 0, n_trav_out_s = 0;   // traveling out-flow modes (rows of P)
+    int m_in_d = 0, m_in_s = 0;               // injected (traveling in-flow) modes
+    int status = 0;                            // PWQT_ST_* bits
+    DBuf sigma_d, sigma_s;                     // n x n row-major complex128
+    DBuf P_d, P_s;                             // rows of B^-1 for traveling out-flow modes
+    DBuf v_out_d, v_out_s;                     // |dE/dk| of those modes (double)
+    DBuf rhs_d, rhs_s;                         // n x m injection vectors (row-major)
+    DBuf cin_s;                                // n x m_s injected source modes (for R)
+    DBuf v_in_d, v_in_s;                       // |dE/dk| of injected modes
+    DBuf sigma_d32, sigma_s32, rhs_d32, rhs_s32;   // complex64 copies (mixed path)
+    size_t bytes() const;
+};
+
+struct System {
+    int N = 0;
+    double Us = 0, Ud = 0;
+    std::vector<double> U;
+    DBuf HV0, HV1;        // N and N-1 blocks: H_ii + V_ii, H_{i,i+1} + V_{i,i+1} (complex128)
+    DBuf HV0f, HV1f;      // complex64 copies (mixed path)
+};
+
+}  // namespace pwqt
+
+struct pwqt_ctx {
+    int dev = 0;
+    pwqt_opts opts{};
+    cudaStream_t stream = nullptr;
+    cublasHandle_t blas = nullptr;
+    cusolverDnHandle_t sol = nullptr;
+    cusolverDnParams_t prm = nullptr;
+    std::string err;
+    long long launches = 0;
+    int sm_count = 0;
+    // basis
+    int n = 0, n_bands = 0;
+    double Lz = 0, Lx = 0;
+    std::vector<double> eps;               // 2 n_bands
+    pwqt::DBuf H0, H1, M0, M1, W;          // n x n row-major complex128; W: 6 blocks
+    pwqt::DBuf M0f, M1f, H0f, H1f;         // complex64 copies
+    std::map<int, pwqt::System> systems;
+    std::map<double, std::unique_ptr<pwqt::LeadEntry>> cache;
+    // scratch reused across calls
+    pwqt::DBuf work_a, work_b;
+};
+
+namespace pwqt {
+// error helpers
+int fail(pwqt_ctx* c, int code, const std::string& msg);
+int cuda_fail(pwqt_ctx* c, cudaError_t e, const char* what);
+
+#define PWQT_CUDA(ctx, x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return ::pwqt::cuda_fail(ctx, e_, #x); } while (0)
+#define PWQT_SOLVER(ctx, x) do { cusolverStatus_t e_ = (x); if (e_ != CUSOLVER_STATUS_SUCCESS) return ::pwqt::fail(ctx, PWQT_ERR_CUDA, std::string("cusolver ") + std::to_string((int)e_) + ": " #x); } while (0)
+#define PWQT_BLAS(ctx, x) do { cublasStatus_t e_ = (x); if (e_ != CUBLAS_STATUS_SUCCESS) return ::pwqt::fail(ctx, PWQT_ERR_CUDA, std::string("cublas ") + std::to_string((int)e_) + ": " #x); } while (0)
+#define PWQT_TRY(x) do { int r_ = (x); if (r_ != PWQT_OK) return r_; } while (0)
+
+int alloc(pwqt_ctx* c, DBuf& b, size_t bytes);
+
+// assembly (assemble.cu)
+int assemble_from_basis(pwqt_ctx* c, const pwqt_cell* cell, int n_bands, const double* eps_host,
+                        const int* n_pw, const int* mx, const int* mz, const double2* coef_dev_rowmajor);
+int epm_basis(pwqt_ctx* c, const pwqt_cell* cell, const pwqt_formfactor* ff, double gcut, int n_bands);
+int build_system_blocks(pwqt_ctx* c, System& s);
+
+// leads (lead.cu)
+int lead_entry(pwqt_ctx* c, double Ec, LeadEntry** out);
+
+// solve (solve.cu)
+struct SolveOut {
+    double *T, *R, *T_ds, *node_n, *resid;
+    int *n_open, *iters, *status;
+};
+int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E_host, int precision,
+                const SolveOut& dev_out, cudaStream_t st);
+
+// small kernels (util.cu)
+void transpose_c128(const double2* in, double2* out, int rows, int cols, cudaStream_t st);
+void c128_to_c64(const double2* in, float2* out, size_t count, cudaStream_t st);
+}  // namespace pwqt

@@ -1,0 +1,262 @@
+// Orchestration of one pwqt_solve call: contact self-energies from the cache,
+// batched block sweeps, FP64 residuals and the observables of Sec. 3.3-3.4
+// (node density, Eq. transmission, reflection) -- all in the library's kernels.
+#include <algorithm>
+#include <cmath>
+
+#include "pwqt_internal.cuh"
+#include "sweep_common.cuh"
+#include "sweep_mixed.cuh"
+
+namespace pwqt {
+
+// ---------------------------------------------------------------- observables
+// T_gamma = sum_{mu traveling out at d} |(P_d c_N)_{mu gamma}|^2 v_mu / v_gamma  (Eq. transmission)
+// R_gamma with the injected part removed at node 1, T_ds for drain-injected modes,
+// node density n[i][c] = sum_{gamma in c} (2/|v_gamma|) sum_alpha |c_{i alpha gamma}|^2.
+__global__ void k_observables(int n, int N, const ObsJob* __restrict__ jobs) {
+    const ObsJob J = jobs[blockIdx.x];
+    const int m = J.ms + J.md;
+    __shared__ double acc[3];
+    if (threadIdx.x < 3) acc[threadIdx.x] = 0.0;
+    __syncthreads();
+    const double2* cN = J.C + (size_t)(N - 1) * J.node_stride;
+    const double2* c1 = J.C;
+    double t_loc = 0, r_loc = 0, tds_loc = 0;
+    // transmission s -> d
+    for (int t = threadIdx.x; t < J.ntd * J.ms; t += blockDim.x) {
+        int mu = t / J.ms, g = t % J.ms;
+        double2 a = make_double2(0, 0);
+        for (int k = 0; k < n; ++k) cfma(a, J.P_d[(size_t)mu * n + k], cN[(size_t)k * J.row_stride + g]);
+        t_loc += cnorm2(a) * J.v_out_d[mu] / J.v_in_s[g];
+    }
+    // reflection at s and transmission d -> s
+    for (int t = threadIdx.x; t < J.nts * m; t += blockDim.x) {
+        int mu = t / m, g = t % m;
+        double2 a = make_double2(0, 0);
+        for (int k = 0; k < n; ++k) {
+            double2 v = c1[(size_t)k * J.row_stride + g];
+            if (g < J.ms) v = csub(v, J.cin_s[(size_t)k * J.ms + g]);
+            cfma(a, J.P_s[(size_t)mu * n + k], v);
+        }
+        if (g < J.ms) r_loc += cnorm2(a) * J.v_out_s[mu] / J.v_in_s[g];
+        else tds_loc += cnorm2(a) * J.v_out_s[mu] / J.v_in_d[g - J.ms];
+    }
+    atomicAdd(&acc[0], t_loc);
+    atomicAdd(&acc[1], r_loc);
+    atomicAdd(&acc[2], tds_loc);
+    // node densities
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double2* ci = J.C + (size_t)i * J.node_stride;
+        double ns = 0, nd = 0;
+        for (int r = 0; r < n; ++r)
+            for (int g = 0; g < m; ++g) {
+                double v = cnorm2(ci[(size_t)r * J.row_stride + g]);
+                if (g < J.ms) ns += v * 2.0 / J.v_in_s[g];
+                else nd += v * 2.0 / J.v_in_d[g - J.ms];
+            }
+        J.node_n[2 * i] = ns;
+        J.node_n[2 * i + 1] = nd;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *J.T = acc[0];
+        *J.R = acc[1];
+        *J.T_ds = acc[2];
+    }
+}
+
+void launch_observables(int n, int N, const ObsJob* jobs, int nb, cudaStream_t st) {
+    k_observables<<<nb, 256, 0, st>>>(n, N, jobs);
+}
+
+// ---------------------------------------------------------------- FP64 residual
+// r_i = b_i - (L_i c_{i-1} + D_i c_i + U_i c_{i+1}) (FP64), per column sums of |r|^2 and |b|^2.
+__global__ void k_residual_fp64(SweepSys sys, const ResJob* __restrict__ jobs) {
+    const ResJob J = jobs[blockIdx.y];
+    const int n = sys.n, N = sys.N, m = J.ms + J.md;
+    const int i = blockIdx.x;
+    if (m == 0) return;
+    const double E = J.E;
+    const double2* ci = J.C + (size_t)i * J.node_stride;
+    const double2* cm1 = i > 0 ? J.C + (size_t)(i - 1) * J.node_stride : nullptr;
+    const double2* cp1 = i < N - 1 ? J.C + (size_t)(i + 1) * J.node_stride : nullptr;
+    const double2* HV0 = sys.HV0 + (size_t)i * n * n;
+    const double2* HV1 = sys.HV1 + (size_t)i * n * n;
+    const double2* HVm = i > 0 ? sys.HV1 + (size_t)(i - 1) * n * n : nullptr;
+    for (int t = threadIdx.x; t < n * m; t += blockDim.x) {
+        int r = t / m, g = t % m;
+        double2 acc = make_double2(0, 0);
+        for (int k = 0; k < n; ++k) {
+            size_t rk = (size_t)r * n + k;
+            double2 d = csub(cscale(sys.M0[rk], E), HV0[rk]);
+            if (i == 0) d = csub(d, J.sig_s[rk]);
+            if (i == N - 1) d = csub(d, J.sig_d[rk]);
+            cfma(acc, d, ci[(size_t)k * J.row_stride + g]);
+            if (cp1) cfma(acc, csub(cscale(sys.M1[rk], E), HV1[rk]), cp1[(size_t)k * J.row_stride + g]);
+            if (cm1) {
+                size_t kr = (size_t)k * n + r;
+                cfma(acc, cconj(csub(cscale(sys.M1[kr], E), HVm[kr])), cm1[(size_t)k * J.row_stride + g]);
+            }
+        }
+        double2 b = make_double2(0, 0);
+        if (i == 0 && g < J.ms) b = J.rhs_s[(size_t)r * J.ms + g];
+        if (i == N - 1 && g >= J.ms) b = J.rhs_d[(size_t)r * J.md + (g - J.ms)];
+        double2 res = csub(b, acc);
+        if (J.Rout) J.Rout[(size_t)i * J.r_node_stride + (size_t)r * J.r_row_stride + g] = res;
+        atomicAdd(&J.rn2[g], cnorm2(res));
+        atomicAdd(&J.bn2[g], cnorm2(b));
+    }
+}
+
+__global__ void k_residual_finish(const ResJob* __restrict__ jobs, int nb) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const ResJob J = jobs[b];
+    int m = J.ms + J.md;
+    double worst = 0.0;
+    for (int g = 0; g < m; ++g) {
+        double bb = J.bn2[g];
+        double v = bb > 0 ? sqrt(J.rn2[g] / bb) : sqrt(J.rn2[g]);
+        worst = fmax(worst, v);
+    }
+    *J.resid = worst;
+}
+
+void launch_residual_fp64(const SweepSys& sys, const ResJob* jobs, int nb, cudaStream_t st) {
+    dim3 grid(sys.N, nb);
+    k_residual_fp64<<<grid, 256, 0, st>>>(sys, jobs);
+    k_residual_finish<<<(nb + 127) / 128, 128, 0, st>>>(jobs, nb);
+}
+
+__global__ void k_fill_int(int* p, int v, int cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cnt) p[i] = v;
+}
+
+// ---------------------------------------------------------------- orchestration
+int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, const SolveOut& o, cudaStream_t st) {
+    const int n = c->n, N = s.N;
+    const size_t nn = (size_t)n * n;
+    // 1. contact data (FP64 cache, computed on a miss)
+    std::vector<LeadEntry*> ls(nE), ld(nE);
+    for (int e = 0; e < nE; ++e) {
+        PWQT_TRY(lead_entry(c, E[e] - s.Us, &ls[e]));
+        PWQT_TRY(lead_entry(c, E[e] - s.Ud, &ld[e]));
+    }
+    std::vector<int> ms(nE), md(nE), hst(nE);
+    for (int e = 0; e < nE; ++e) {
+        hst[e] = ls[e]->status | ld[e]->status;
+        bool ok = !(hst[e] & PWQT_ST_MODE_COUNT);
+        ms[e] = ok ? ls[e]->m_in_s : 0;
+        md[e] = ok ? ld[e]->m_in_d : 0;
+    }
+    // 2. batches bounded by the device budget
+    size_t free_b = 0, total_b = 0;
+    PWQT_CUDA(c, cudaMemGetInfo(&free_b, &total_b));
+    size_t budget = c->opts.hbm_budget_bytes ? c->opts.hbm_budget_bytes : (size_t)(0.85 * (double)free_b);
+    auto per_energy = [&](int e) {
+        int m = ms[e] + md[e];
+        size_t b = sizeof(double2) * ((size_t)N * n * (n + m) + nn) + 64 * sizeof(double) * (m + 2);
+        if (precision == PWQT_MIXED) b += mixed_bytes_per_energy(n, N, m);
+        return b;
+    };
+    SweepSys sys{n, N, c->M0.as<double2>(), c->M1.as<double2>(), s.HV0.as<double2>(), s.HV1.as<double2>()};
+    PWQT_BLAS(c, cublasSetStream(c->blas, st));
+    int e0 = 0;
+    while (e0 < nE) {
+        int nb = 0;
+        size_t need = 0;
+        int cap = c->opts.batch > 0 ? c->opts.batch : 1 << 30;
+        while (e0 + nb < nE && nb < cap) {
+            size_t pe = per_energy(e0 + nb);
+            if (nb > 0 && need + pe > budget) break;
+            need += pe;
+            ++nb;
+        }
+        if (need > budget) return fail(c, PWQT_ERR_OOM, "one energy needs " + std::to_string(need) + " bytes, budget " + std::to_string(budget));
+        // workspace
+        std::vector<size_t> off(nb + 1, 0);
+        for (int b = 0; b < nb; ++b) off[b + 1] = off[b] + (size_t)N * n * (n + ms[e0 + b] + md[e0 + b]);
+        size_t maxm = 1;
+        for (int b = 0; b < nb; ++b) maxm = std::max<size_t>(maxm, ms[e0 + b] + md[e0 + b]);
+        DBuf XY, Sb, jobs_d, obs_d, res_d, norms;
+        PWQT_TRY(alloc(c, XY, sizeof(double2) * std::max<size_t>(off[nb], 1)));
+        PWQT_TRY(alloc(c, Sb, sizeof(double2) * nn * nb));
+        PWQT_TRY(alloc(c, norms, sizeof(double) * 2 * nb * maxm));
+        PWQT_CUDA(c, cudaMemsetAsync(norms.p, 0, norms.bytes, st));
+        std::vector<SweepJob> jobs(nb);
+        std::vector<ObsJob> obs(nb);
+        std::vector<ResJob> res(nb);
+        for (int b = 0; b < nb; ++b) {
+            int e = e0 + b;
+            LeadEntry *Ls = ls[e], *Ld = ld[e];
+            int m = ms[e] + md[e];
+            SweepJob& J = jobs[b];
+            J.E = E[e];
+            J.ms = ms[e];
+            J.md = md[e];
+            J.sig_s = Ls->sigma_s.as<double2>();
+            J.sig_d = Ld->sigma_d.as<double2>();
+            J.rhs_s = Ls->rhs_s.as<double2>();
+            J.rhs_d = Ld->rhs_d.as<double2>();
+            J.XY = XY.as<double2>() + off[b];
+            J.S = Sb.as<double2>() + nn * b;
+            J.status = o.status + e;
+            ObsJob& O = obs[b];
+            O.ms = ms[e]; O.md = md[e];
+            O.ntd = (hst[e] & PWQT_ST_MODE_COUNT) ? 0 : Ld->n_trav_out_d;
+            O.nts = (hst[e] & PWQT_ST_MODE_COUNT) ? 0 : Ls->n_trav_out_s;
+            O.C = J.XY + n;
+            O.node_stride = (size_t)n * (n + m);
+            O.row_stride = n + m;
+            O.P_d = Ld->P_d.as<double2>(); O.P_s = Ls->P_s.as<double2>();
+            O.v_out_d = Ld->v_out_d.as<double>(); O.v_out_s = Ls->v_out_s.as<double>();
+            O.v_in_d = Ld->v_in_d.as<double>(); O.v_in_s = Ls->v_in_s.as<double>();
+            O.cin_s = Ls->cin_s.as<double2>();
+            O.T = o.T + e; O.R = o.R + e; O.T_ds = o.T_ds + e; O.node_n = o.node_n + (size_t)e * N * 2;
+            ResJob& Rj = res[b];
+            Rj.E = E[e]; Rj.ms = ms[e]; Rj.md = md[e];
+            Rj.sig_s = J.sig_s; Rj.sig_d = J.sig_d; Rj.rhs_s = J.rhs_s; Rj.rhs_d = J.rhs_d;
+            Rj.C = O.C; Rj.node_stride = O.node_stride; Rj.row_stride = O.row_stride;
+            Rj.Rout = nullptr; Rj.r_node_stride = 0; Rj.r_row_stride = 0;
+            Rj.rn2 = norms.as<double>() + 2 * maxm * b;
+            Rj.bn2 = Rj.rn2 + maxm;
+            Rj.resid = o.resid + e;
+        }
+        // statuses from the contacts
+        for (int b = 0; b < nb; ++b)
+            PWQT_CUDA(c, cudaMemcpyAsync(o.status + e0 + b, &hst[e0 + b], sizeof(int), cudaMemcpyHostToDevice, st));
+        PWQT_TRY(alloc(c, jobs_d, sizeof(SweepJob) * nb));
+        PWQT_TRY(alloc(c, obs_d, sizeof(ObsJob) * nb));
+        PWQT_TRY(alloc(c, res_d, sizeof(ResJob) * nb));
+        PWQT_CUDA(c, cudaMemcpyAsync(jobs_d.p, jobs.data(), sizeof(SweepJob) * nb, cudaMemcpyHostToDevice, st));
+        PWQT_CUDA(c, cudaMemcpyAsync(obs_d.p, obs.data(), sizeof(ObsJob) * nb, cudaMemcpyHostToDevice, st));
+        PWQT_CUDA(c, cudaMemcpyAsync(res_d.p, res.data(), sizeof(ResJob) * nb, cudaMemcpyHostToDevice, st));
+        if (precision == PWQT_MIXED) {
+            PWQT_TRY(solve_mixed(c, s, sys, jobs, jobs_d.as<SweepJob>(), res, res_d.as<ResJob>(), nb, o.iters + e0, st));
+        } else {
+            launch_sweep_fp64(sys, jobs_d.as<SweepJob>(), nb, st);
+            c->launches++;
+            PWQT_CUDA(c, cudaGetLastError());
+            launch_residual_fp64(sys, res_d.as<ResJob>(), nb, st);
+            c->launches += 2;
+            if (o.iters) {
+                k_fill_int<<<(nb + 127) / 128, 128, 0, st>>>(o.iters + e0, 0, nb);
+                c->launches++;
+            }
+        }
+        launch_observables(n, N, obs_d.as<ObsJob>(), nb, st);
+        c->launches++;
+        PWQT_CUDA(c, cudaGetLastError());
+        // n_open (source, drain) per energy
+        std::vector<int> nopen(2 * nb);
+        for (int b = 0; b < nb; ++b) { nopen[2 * b] = ms[e0 + b]; nopen[2 * b + 1] = md[e0 + b]; }
+        if (o.n_open) PWQT_CUDA(c, cudaMemcpyAsync(o.n_open + 2 * e0, nopen.data(), sizeof(int) * 2 * nb, cudaMemcpyHostToDevice, st));
+        PWQT_CUDA(c, cudaStreamSynchronize(st));
+        e0 += nb;
+    }
+    return PWQT_OK;
+}
+
+}  // namespace pwqt

@@ -1,0 +1,48 @@
+// Work descriptors shared by the sweep, residual and observable kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace pwqt {
+
+// Per-system data of the block-tridiagonal matrix (complex128, row-major n x n blocks).
+struct SweepSys {
+    int n, N;
+    const double2* M0;    // M_ii
+    const double2* M1;    // M_{i,i+1}
+    const double2* HV0;   // N blocks H_ii + V_ii
+    const double2* HV1;   // N-1 blocks H_{i,i+1} + V_{i,i+1}
+};
+
+// One energy of a batch.
+struct SweepJob {
+    double E;
+    int ms, md;                 // injected modes from source / drain (m = ms + md columns)
+    const double2* sig_s;       // n x n
+    const double2* sig_d;
+    const double2* rhs_s;       // n x ms, row-major
+    const double2* rhs_d;       // n x md
+    double2* XY;                // N x n x (n + m): [X_i | y_i], y overwritten by c_i
+    double2* S;                 // n x n scratch
+    int* status;
+};
+
+// Reduction descriptors of one energy (observables of Eq. transmission and Sec. 3.3).
+struct ObsJob {
+    int ms, md, ntd, nts;
+    const double2* C;           // c: node i at C + i*node_stride, row r at + r*row_stride
+    size_t node_stride;
+    int row_stride;
+    const double2* P_d;         // ntd x n
+    const double2* P_s;         // nts x n
+    const double* v_out_d;      // ntd
+    const double* v_out_s;      // nts
+    const double* v_in_d;       // md
+    const double* v_in_s;       // ms
+    const double2* cin_s;       // n x ms
+    double* T; double* R; double* T_ds; double* node_n;   // node_n: N x 2
+};
+
+void launch_sweep_fp64(const SweepSys& sys, const SweepJob* jobs, int nb, cudaStream_t st);
+void launch_observables(int n, int N, const ObsJob* jobs, int nb, cudaStream_t st);
+
+}  // namespace pwqt

@@ -1,0 +1,35 @@
+// Mixed-precision path: complex64 block sweep on the tensor cores + FP64 refinement.
+#pragma once
+#include <vector>
+
+#include "pwqt_internal.cuh"
+#include "sweep_common.cuh"
+
+namespace pwqt {
+
+// FP64 residual r = B - A c of one energy (Sec. 3.2 system), optionally written out.
+struct ResJob {
+    double E;
+    int ms, md;
+    const double2* sig_s;
+    const double2* sig_d;
+    const double2* rhs_s;
+    const double2* rhs_d;
+    const double2* C;          // current solution
+    size_t node_stride;
+    int row_stride;
+    double2* Rout;             // residual output (nullable)
+    size_t r_node_stride;
+    int r_row_stride;
+    double* rn2;               // per column sum |r|^2 (m entries, zeroed by the caller)
+    double* bn2;               // per column sum |b|^2
+    double* resid;             // max over columns of ||r|| / ||b||
+};
+
+void launch_residual_fp64(const SweepSys& sys, const ResJob* jobs, int nb, cudaStream_t st);
+
+size_t mixed_bytes_per_energy(int n, int N, int m);
+int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJob>& jobs, SweepJob* jobs_d,
+                std::vector<ResJob>& res, ResJob* res_d, int nb, int* iters_dev, cudaStream_t st);
+
+}  // namespace pwqt

@@ -1,0 +1,213 @@
+"""Thin ctypes binding of libpwqt (include/pwqt.h).
+
+Argument marshalling only: every step of the computation runs in the library's
+CUDA kernels.  The library must have been built (paper_1903_00548_gb300.build);
+loading fails loudly when it is missing or no CUDA device is present.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpwqt.so")
+
+PWQT_OK = 0
+ERR_NAMES = {-1: "INVALID_ARG", -2: "BASIS_TOO_SMALL", -3: "OOM", -4: "CUDA", -5: "STATE", -6: "NO_DEVICE"}
+FP64, MIXED = 0, 1
+ST_SINGULAR_PIVOT, ST_MODE_COUNT, ST_IR_NO_CONVERGE, ST_DEGENERATE, ST_NEAR_UNIT = 1, 2, 4, 8, 16
+
+EXPORTS = ["pwqt_create", "pwqt_destroy", "pwqt_last_error", "pwqt_assemble_intrinsic", "pwqt_set_enhancement",
+           "pwqt_get_blocks", "pwqt_set_extrinsic", "pwqt_solve", "pwqt_solve_dev", "pwqt_prepare_leads",
+           "pwqt_cache_info", "pwqt_bands", "pwqt_kernel_launches"]
+
+
+class PwqtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pwqt error {code} ({ERR_NAMES.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class Opts(C.Structure):
+    _fields_ = [("device", C.c_int), ("hbm_budget_bytes", C.c_size_t), ("ir_tol", C.c_double),
+                ("ir_max_iters", C.c_int), ("batch", C.c_int)]
+
+
+class CellC(C.Structure):
+    _fields_ = [("dim", C.c_int), ("Lz", C.c_double), ("Lx", C.c_double), ("n_atoms", C.c_int),
+                ("atoms", C.POINTER(C.c_double)), ("omega0", C.c_double)]
+
+
+class FormFactorC(C.Structure):
+    _fields_ = [("v0", C.c_double), ("sigma", C.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libpwqt.so (no fallback: raises if the library is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpwqt not built: {path} missing (run python -m paper_1903_00548_gb300.build)")
+    lib = C.CDLL(path)
+    P, I, D, S = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int)
+    lib.pwqt_create.argtypes = [C.POINTER(P), C.POINTER(Opts)]
+    lib.pwqt_destroy.argtypes = [P]
+    lib.pwqt_last_error.argtypes = [P]
+    lib.pwqt_last_error.restype = C.c_char_p
+    lib.pwqt_assemble_intrinsic.argtypes = [P, C.POINTER(CellC), C.POINTER(FormFactorC), D, I, ip]
+    lib.pwqt_set_enhancement.argtypes = [P, C.POINTER(CellC), I, dp, ip, ip, ip, dp, ip]
+    lib.pwqt_get_blocks.argtypes = [P, dp, dp, dp, dp, dp]
+    lib.pwqt_set_extrinsic.argtypes = [P, I, I, dp]
+    lib.pwqt_solve.argtypes = [P, I, I, dp, I, dp, dp, dp, ip, dp, dp, ip, ip]
+    lib.pwqt_solve_dev.argtypes = [P, I, I, dp, I, P, P, P, P, P, P, P, P, P]
+    lib.pwqt_prepare_leads.argtypes = [P, I, I, dp]
+    lib.pwqt_cache_info.argtypes = [P, ip, C.POINTER(S)]
+    lib.pwqt_bands.argtypes = [P, I, dp, dp]
+    lib.pwqt_kernel_launches.argtypes = [P, C.POINTER(C.c_longlong), I]
+    for f in EXPORTS:
+        if f != "pwqt_last_error":
+            getattr(lib, f).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+def _iptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int)) if a is not None else None
+
+
+def _cell(cell):
+    atoms = np.ascontiguousarray(cell.atoms, dtype=np.float64).ravel()
+    c = CellC(cell.dim, cell.Lz, cell.Lx, len(cell.atoms), _dptr(atoms), cell.omega0)
+    return c, atoms
+
+
+@dataclass
+class SolveResult:
+    T: np.ndarray
+    R: np.ndarray
+    T_ds: np.ndarray
+    n_open: np.ndarray      # (n_E, 2)
+    node_n: np.ndarray      # (n_E, N, 2)
+    resid: np.ndarray
+    iters: np.ndarray
+    status: np.ndarray
+
+
+class Context:
+    """One libpwqt context on one CUDA device."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, ir_tol: float = 0.0, ir_max_iters: int = 0,
+                 batch: int = 0):
+        self.lib = load()
+        self.h = C.c_void_p()
+        o = Opts(device, hbm_budget_bytes, ir_tol, ir_max_iters, batch)
+        r = self.lib.pwqt_create(C.byref(self.h), C.byref(o))
+        if r != PWQT_OK:
+            raise PwqtError(r, "pwqt_create failed")
+        self.n = 0
+        self.n_nodes = {}
+
+    def close(self):
+        if self.h:
+            self.lib.pwqt_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, r):
+        if r != PWQT_OK:
+            raise PwqtError(r, self.lib.pwqt_last_error(self.h).decode())
+
+    def assemble_intrinsic(self, cell, ff, gcut: float, n_bands: int) -> int:
+        cc, keep = _cell(cell)
+        f = FormFactorC(ff.v0, ff.sigma)
+        n = C.c_int()
+        self._check(self.lib.pwqt_assemble_intrinsic(self.h, C.byref(cc), C.byref(f), gcut, n_bands, C.byref(n)))
+        self.n = n.value
+        self.n_nodes = {}
+        return self.n
+
+    def set_enhancement(self, cell, eps, groups) -> int:
+        """groups: [(mx, mz, C (n_pw x n_bands complex)), ...] for k = 0 and k = pi/Lz."""
+        cc, keep = _cell(cell)
+        nb = groups[0][2].shape[1]
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        n_pw = np.array([len(g[0]) for g in groups], dtype=np.int32)
+        mx = np.ascontiguousarray(np.concatenate([g[0] for g in groups]), dtype=np.int32)
+        mz = np.ascontiguousarray(np.concatenate([g[1] for g in groups]), dtype=np.int32)
+        coef = np.ascontiguousarray(np.concatenate([g[2] for g in groups], axis=0), dtype=np.complex128)
+        n = C.c_int()
+        self._check(self.lib.pwqt_set_enhancement(self.h, C.byref(cc), nb, _dptr(eps), _iptr(n_pw), _iptr(mx), _iptr(mz),
+                                                  coef.ctypes.data_as(C.POINTER(C.c_double)), C.byref(n)))
+        self.n = n.value
+        self.n_nodes = {}
+        return self.n
+
+    def get_blocks(self):
+        n = self.n
+        H0, H1, M0, M1 = (np.zeros((n, n), np.complex128) for _ in range(4))
+        W = np.zeros((6, n, n), np.complex128)
+        ptr = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        self._check(self.lib.pwqt_get_blocks(self.h, ptr(H0), ptr(H1), ptr(M0), ptr(M1), ptr(W)))
+        return dict(H0=H0, H1=H1, M0=M0, M1=M1, W=W)
+
+    def set_extrinsic(self, sys: int, U):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        self._check(self.lib.pwqt_set_extrinsic(self.h, sys, len(U), _dptr(U)))
+        self.n_nodes[sys] = len(U)
+
+    def prepare_leads(self, sys: int, E):
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        self._check(self.lib.pwqt_prepare_leads(self.h, sys, len(E), _dptr(E)))
+
+    def solve(self, sys: int, E, precision: int = FP64) -> SolveResult:
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        nE, N = len(E), self.n_nodes.get(sys, 0)
+        T, R, Tds, resid = (np.zeros(nE) for _ in range(4))
+        nopen = np.zeros((nE, 2), np.int32)
+        node_n = np.zeros((nE, N, 2))
+        iters = np.zeros(nE, np.int32)
+        status = np.zeros(nE, np.int32)
+        self._check(self.lib.pwqt_solve(self.h, sys, nE, _dptr(E), precision, _dptr(T), _dptr(R), _dptr(Tds), _iptr(nopen),
+                                        _dptr(node_n), _dptr(resid), _iptr(iters), _iptr(status)))
+        return SolveResult(T, R, Tds, nopen, node_n, resid, iters, status)
+
+    def solve_dev(self, sys: int, E, precision: int, out: dict, stream_ptr: int = 0):
+        """Device-buffer variant: `out` maps output names to device pointers (int) or None."""
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        g = lambda k: C.c_void_p(out.get(k)) if out.get(k) else None
+        self._check(self.lib.pwqt_solve_dev(self.h, sys, len(E), _dptr(E), precision, g("T"), g("R"), g("T_ds"),
+                                            g("n_open"), g("node_n"), g("resid"), g("iters"), g("status"),
+                                            C.c_void_p(stream_ptr) if stream_ptr else None))
+
+    def cache_info(self):
+        e, b = C.c_int(), C.c_size_t()
+        self._check(self.lib.pwqt_cache_info(self.h, C.byref(e), C.byref(b)))
+        return e.value, b.value
+
+    def bands(self, k):
+        k = np.ascontiguousarray(k, dtype=np.float64)
+        out = np.zeros((len(k), self.n))
+        self._check(self.lib.pwqt_bands(self.h, len(k), _dptr(k), _dptr(out)))
+        return out
+
+    def kernel_launches(self, reset: bool = False) -> int:
+        v = C.c_longlong()
+        self._check(self.lib.pwqt_kernel_launches(self.h, C.byref(v), 1 if reset else 0))
+        return v.value
