@@ -1,0 +1,363 @@
+"""Benchmark: energy-solves/s of the per-energy open-boundary solve at block size 512.
+
+Workload (default): the 1.5 nm armchair ribbon at G_cut = 60 nm^-1, block n = 512
+(256 Bloch waves at Gamma and at Z), N = 200 nodes, a seeded smooth potential
+<= 0.3 eV, and the 1024-point energy grid [E_cb - 0.1, E_cb + 1.0] eV; one step
+solves one batch of energies of that grid (contact self-energies resident in the
+cache, built before timing and reported separately as sigma_cold_s_per_energy).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                [--precision mixed|fp64|auto] [--batch B]
+Under torchrun every rank solves its own batch (weak scaling, no data-path
+collective); the timed region is bracketed by a barrier and synchronize and the
+max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "energy-solves/s at block 512 (FP64 vs mixed+refine, <=1e-8 in T); p50/p99 latency"
+UNIT = "energy-solves/s"
+L2_BYTES = 129 * 2 ** 20
+# nominal dense rates of GB300 used to scale the measured bf16 peak to other dtypes
+NOMINAL_TFLOPS = {"bf16": 2250.0, "tf32": 1100.0, "f64": 1.25}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p.get("bf16_tflops", 1900.0), p.get("hbm_gbs", 6800.0), "measured"
+    except Exception:
+        return 1900.0, 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    def __init__(self, device: int, path: str):
+        self.path = path
+        self.proc = None
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(device), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle sample
+ORACLE_SAMPLE_NODES = 8
+
+
+def _oracle_sample(conn, wl_name, n_nodes_full, reps):
+    """Times the oracle (as it stands) on one energy of the workload with the
+    device shortened to ORACLE_SAMPLE_NODES nodes; its banded LU costs O(N), so the
+    time of a full-length solve is t * N_full / N_sample.  One BLAS thread."""
+    try:
+        os.environ["OPENBLAS_NUM_THREADS"] = "1"
+        os.environ["OMP_NUM_THREADS"] = "1"
+        os.environ["MKL_NUM_THREADS"] = "1"
+        from oracle import pwqt_oracle as O
+        from paper_1903_00548_gb300 import workloads as W
+        wl = getattr(W, wl_name)()
+        U = W.random_smooth(ORACLE_SAMPLE_NODES)
+        s = O.build_system(wl.cell, wl.ff, wl.gcut, wl.n_bands, U)
+        E = float(wl.energies[len(wl.energies) // 2])
+        contacts = O.contacts_at(s.blk, E, U[0], U[-1])
+        times = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            O.solve_energy(s.blk, s.Vd, s.Vu, s.U, E, contacts=contacts)
+            times.append(time.perf_counter() - t0)
+        t_full = min(times) * n_nodes_full / ORACLE_SAMPLE_NODES
+        conn.send({"ok": True, "t_sample": min(times), "times": times, "t_full": t_full,
+                   "m": int(contacts[0].c_in.shape[1] + contacts[1].c_in.shape[1])})
+    except Exception as e:  # pragma: no cover - reported in the JSON line
+        conn.send({"ok": False, "error": repr(e)})
+    conn.close()
+
+
+def start_oracle_sample(wl_name, n_nodes_full, reps=3):
+    ctx = mp.get_context("spawn")
+    a, b = ctx.Pipe(duplex=False)
+    p = ctx.Process(target=_oracle_sample, args=(b, wl_name, n_nodes_full, reps), daemon=True)
+    p.start()
+    return p, a
+
+
+def finish_oracle_sample(p, conn, timeout=900):
+    if conn.poll(timeout):
+        r = conn.recv()
+    else:
+        r = {"ok": False, "error": "oracle sample timed out"}
+    p.join(timeout=5)
+    if p.is_alive():
+        p.kill()
+    return r
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    from paper_1903_00548_gb300 import workloads as W
+    wl = getattr(W, args.workload)()
+    p, conn = start_oracle_sample(args.workload, wl.n_nodes, reps=args.warmup + args.steps)
+    r = finish_oracle_sample(p, conn)
+    if not r.get("ok"):
+        print(json.dumps({"impl": "reference", "unavailable": r.get("error", "oracle failed")}))
+        return 0
+    ts = r["times"][args.warmup:] or r["times"]
+    t_full = statistics.mean(ts) * wl.n_nodes / ORACLE_SAMPLE_NODES
+    value = 1.0 / t_full
+    sample = (f"one energy of {args.workload} (n={wl.n}) on {ORACLE_SAMPLE_NODES} of {wl.n_nodes} nodes per step, "
+              f"banded-LU time scaled by {wl.n_nodes}/{ORACLE_SAMPLE_NODES}; contact self-energies built before timing")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_full,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "n": wl.n, "nodes": wl.n_nodes},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value, "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_1903_00548_gb300 import build as B
+    from paper_1903_00548_gb300 import pwqt as pw
+    from paper_1903_00548_gb300 import workloads as W
+
+    B.build()
+    wl = getattr(W, args.workload)()
+    if args.nodes:
+        wl.n_nodes = args.nodes
+        wl.U = W.random_smooth(args.nodes)
+    prec_name = args.precision
+    if prec_name == "auto":
+        prec_name = "mixed"
+    prec = pw.MIXED if prec_name == "mixed" else pw.FP64
+    batch = args.batch or (152 if prec == pw.FP64 else 304)
+    n_grid = len(wl.energies)
+    idx = (np.arange(batch) * max(1, n_grid // batch) + rank * batch) % n_grid
+    E = np.sort(wl.energies[idx])
+
+    oracle_proc = None
+    if rank == 0 and not args.no_cpu_baseline:
+        oracle_proc = start_oracle_sample(args.workload, wl.n_nodes)
+
+    torch.cuda.set_device(local)
+    ctx = pw.Context(device=local)
+    t0 = time.perf_counter()
+    n = ctx.assemble_intrinsic(wl.cell, wl.ff, wl.gcut, wl.n_bands)
+    ctx.set_extrinsic(0, wl.U)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ctx.prepare_leads(0, E)
+    t_leads = time.perf_counter() - t0
+
+    dev = torch.device("cuda", local)
+    N = wl.n_nodes
+    outs = {
+        "T": torch.empty(batch, dtype=torch.float64, device=dev),
+        "R": torch.empty(batch, dtype=torch.float64, device=dev),
+        "T_ds": torch.empty(batch, dtype=torch.float64, device=dev),
+        "n_open": torch.empty(2 * batch, dtype=torch.int32, device=dev),
+        "node_n": torch.empty(batch * N * 2, dtype=torch.float64, device=dev),
+        "resid": torch.empty(batch, dtype=torch.float64, device=dev),
+        "iters": torch.empty(batch, dtype=torch.int32, device=dev),
+        "status": torch.empty(batch, dtype=torch.int32, device=dev),
+    }
+    ptrs = {k: v.data_ptr() for k, v in outs.items()}
+    stream = torch.cuda.Stream(device=dev)
+
+    def step():
+        ctx.solve_dev(0, E, prec, ptrs, stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    ctx.profile(True, reset=True)
+    launches0 = ctx.kernel_launches()
+    clocks = Clocks(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+                    if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/pwqt_clocks_{rank}.csv")
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    ev_s = torch.cuda.Event(enable_timing=True)
+    ev_e = torch.cuda.Event(enable_timing=True)
+    step_ms = []
+    ev_s.record(stream)
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        step_ms.append((a, b))
+    ev_e.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    total_ms = ev_s.elapsed_time(ev_e)
+    per_step = [a.elapsed_time(b) for a, b in step_ms]
+    launches = (ctx.kernel_launches() - launches0) // max(1, args.steps)
+    sweep_ms, sweep_n, sweep_flops = ctx.profile(False)
+    total_ms = max_over_ranks(world, total_ms)
+    value = world * batch * args.steps / (total_ms / 1e3)
+
+    # results of the last step: statuses, refinement, residuals
+    status = outs["status"].cpu().numpy()
+    iters = outs["iters"].cpu().numpy()
+    resid = outs["resid"].cpu().numpy()
+    nopen = outs["n_open"].cpu().numpy().reshape(batch, 2)
+
+    # end to end through the host-buffer C ABI (copies inside the timed region)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        res = ctx.solve(0, E, prec)
+    t_e2e = time.perf_counter() - t0
+    t_e2e = max_over_ranks(world, t_e2e)
+    e2e_value = world * batch * e2e_steps / t_e2e
+    h2d = 8 * batch
+    d2h = batch * (8 * 4 + 4 * 4 + 8 * 2 * N)
+
+    # roofline of the dominant kernel (the block sweep)
+    bf16, hbm, src = peaks()
+    dtype = "f64" if prec == pw.FP64 else "tf32"
+    peak = bf16 * NOMINAL_TFLOPS[dtype] / NOMINAL_TFLOPS["bf16"]
+    achieved = (sweep_flops / max(sweep_n, 1)) / (sweep_ms / max(sweep_n, 1) / 1e3) / 1e12 if sweep_n else None
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "kernel": "k_sweep_fp64" if prec == pw.FP64 else "mixed block sweep",
+            "peak_source": f"{src} bf16 x nominal {dtype}/bf16 ratio",
+            "flops_per_launch": sweep_flops / max(sweep_n, 1), "avg_launch_ms": sweep_ms / max(sweep_n, 1),
+            "launches": sweep_n}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == pw.FP64 else "c64/tf32+f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "nodes": N, "energies_per_step": batch,
+                       "energy_grid": n_grid, "precision": prec_name, "l2": "inputs larger than L2 "
+                       f"(factor panels {N * n * n * 16 * batch / 1e9:.0f} GB per step)"},
+            "latency_ms": {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99)),
+                           "unit": f"per step of {batch} energies"},
+            "sigma_cold_s_per_energy": t_leads / max(1, len(set(E.tolist()))), "setup_s": t_setup,
+            "gpu_launches": int(launches), "clocks": clk, "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "results": {"max_resid": float(np.max(resid)), "max_iters": int(np.max(iters)),
+                        "status_nonzero": int(np.count_nonzero(status)), "mean_modes": float(nopen.sum(1).mean()),
+                        "T_mean": float(np.mean(res.T))}}
+    if oracle_proc is not None:
+        r = finish_oracle_sample(*oracle_proc)
+        if r.get("ok"):
+            line["cpu_baseline"] = {"value": 1.0 / r["t_full"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"one energy of {args.workload} on {ORACLE_SAMPLE_NODES} of {N} "
+                                              f"nodes, banded-LU time scaled by {N}/{ORACLE_SAMPLE_NODES} "
+                                              f"(t_sample {r['t_sample']:.2f} s), self-energies built untimed"}
+        else:
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": "failed: " + r.get("error", "?")}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64"])
+    ap.add_argument("--workload", default="ribbon512")
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--nodes", type=int, default=0, help="development only: shorter device")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -46,7 +46,7 @@ typedef struct pwqt_ctx pwqt_ctx;
 #define PWQT_ST_MODE_COUNT       2    /* out-flow mode count != n at a contact     */
 #define PWQT_ST_IR_NO_CONVERGE   4    /* refinement hit its iteration limit        */
 #define PWQT_ST_DEGENERATE       8    /* degenerate traveling modes at a contact   */
-#define PWQT_ST_NEAR_UNIT        16   /* an evanescent |lambda| within 1e-5 of 1   */
+#define PWQT_ST_NEAR_UNIT        16   /* an evanescent |lambda| within 1e-3 of 1   */
 
 /* precision of the block sweep */
 #define PWQT_FP64                0    /* complex128 throughout                     */
@@ -185,6 +185,18 @@ int pwqt_cache_info(pwqt_ctx* ctx, int* entries, size_t* bytes);
  * ascending per k'.
  */
 int pwqt_bands(pwqt_ctx* ctx, int n_k, const double* k, double* E_out);
+
+/*
+ * CUDA-event timing of the block-sweep kernels (the dominant cost, Sec. 3.2
+ * system): with enable != 0 every sweep launch is bracketed by events on the
+ * stream it runs on and its duration is accumulated.  Outputs (any may be NULL):
+ * total milliseconds, number of timed launches, and the algorithmic flops of those
+ * launches, (56/3) N n^3 real flops per energy (complex LU 8/3 n^3 + solve for
+ * X_i 8 n^3 + Schur product 8 n^3 per node).  reset != 0 zeroes the counters after
+ * reading them.  Timing serialises the host with each sweep launch.
+ */
+int pwqt_profile(pwqt_ctx* ctx, int enable, double* sweep_ms, long long* sweep_launches,
+                 double* sweep_flops, int reset);
 
 /* Launch counters of the library's own kernels since the last reset. */
 int pwqt_kernel_launches(pwqt_ctx* ctx, long long* count, int reset);

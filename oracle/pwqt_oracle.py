@@ -39,7 +39,7 @@ reason in the design notes):
     "-hbar^2/m ... + h.c." of Sec. 2.3 is read as that symmetrised sum.
   * lambda is the ratio (outside neighbour)/(edge node); drain lambda_d =
     c_{i+1}/c_i, source lambda_s = c_{i-1}/c_i = 1/lambda_d with the same c.
-  * traveling iff ||lambda| - 1| < 1e-6 on the generalised-QZ eigenvalues;
+  * traveling iff ||lambda| - 1| < 1e-4 on the generalised-QZ eigenvalues;
     each traveling mode is then refined on the unit circle (Newton on k with
     the band structure of Sec. 5.1 and the Hellmann-Feynman slope), so that
     |lambda| = 1 holds to rounding as Sec. 3.1 states for exact arithmetic.
@@ -61,7 +61,7 @@ import numpy as np
 import scipy.linalg as sla
 
 HB2M = 0.0380998212          # hbar^2/(2 m_e), eV nm^2
-TRAVEL_TOL = 1e-6            # ||lambda| - 1| below which a mode is traveling
+TRAVEL_TOL = 1e-4            # ||lambda| - 1| below which a mode is traveling
 DEGEN_TOL = 1e-8             # |lambda_a - lambda_b| below which traveling modes are degenerate
 
 

@@ -38,6 +38,11 @@ int alloc(pwqt_ctx* c, DBuf& b, size_t bytes) {
     return PWQT_OK;
 }
 
+int ensure(pwqt_ctx* c, DBuf& b, size_t bytes) {
+    if (b.bytes >= bytes && b.p) return PWQT_OK;
+    return alloc(c, b, bytes + bytes / 8);
+}
+
 // ---------------------------------------------------------------- small utilities
 __global__ void k_transpose_c128(const double2* __restrict__ in, double2* __restrict__ out, int rows, int cols) {
     __shared__ double2 t[32][33];

@@ -8,7 +8,7 @@
 //        lambda = (1 + mu)/(1 - mu),
 //     which keeps the transformed spectrum bounded when lambda spans many decades,
 //     and C is diagonalised by cuSOLVER's non-Hermitian eigensolver.
-//  2. Modes with ||lambda| - 1| < 1e-6 are traveling; each is refined onto the unit
+//  2. Modes with ||lambda| - 1| < 1e-4 are traveling; each is refined onto the unit
 //     circle: with lambda = e^{ikL}, Ec is an eigenvalue of H(k) c = E M(k) c, so
 //     Newton on k with the Hellmann-Feynman slope (Eq. hellmann-feynman) and shifted
 //     inverse iteration for c converge to |lambda| = 1 exactly.
@@ -17,7 +17,9 @@
 //     B_s (|lambda_d| > 1 or dE/dk < 0, lambda_s = 1/lambda_d); Sigma = K' B Lambda B^-1
 //     with K'_d = K+, K'_s = K-; injection vectors B_gamma = (K' lambda_gamma - Sigma) c_gamma.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <thread>
 
 #include "pwqt_internal.cuh"
 
@@ -203,52 +205,53 @@ struct LinSolve {
     std::vector<char> hwork;
 };
 
-int lu_solve(pwqt_ctx* c, LinSolve& ls, int n, double2* A, double2* B, int nrhs) {
+int lu_solve(pwqt_ctx* c, const LeadWorker& wk, LinSolve& ls, int n, double2* A, double2* B, int nrhs) {
     size_t wd = 0, wh = 0;
-    PWQT_SOLVER(c, cusolverDnXgetrf_bufferSize(c->sol, c->prm, n, n, CUDA_C_64F, A, n, CUDA_C_64F, &wd, &wh));
+    PWQT_SOLVER(c, cusolverDnXgetrf_bufferSize(wk.sol, wk.prm, n, n, CUDA_C_64F, A, n, CUDA_C_64F, &wd, &wh));
     if (ls.work.bytes < wd) PWQT_TRY(alloc(c, ls.work, wd));
     if (ls.ipiv.bytes < sizeof(int64_t) * n) PWQT_TRY(alloc(c, ls.ipiv, sizeof(int64_t) * n));
     if (!ls.info.p) PWQT_TRY(alloc(c, ls.info, sizeof(int)));
     if (ls.hwork.size() < wh + 16) ls.hwork.resize(wh + 16);
-    PWQT_SOLVER(c, cusolverDnXgetrf(c->sol, c->prm, n, n, CUDA_C_64F, A, n, ls.ipiv.as<int64_t>(), CUDA_C_64F, ls.work.p,
+    PWQT_SOLVER(c, cusolverDnXgetrf(wk.sol, wk.prm, n, n, CUDA_C_64F, A, n, ls.ipiv.as<int64_t>(), CUDA_C_64F, ls.work.p,
                                     wd, ls.hwork.data(), wh, ls.info.as<int>()));
-    PWQT_SOLVER(c, cusolverDnXgetrs(c->sol, c->prm, CUBLAS_OP_N, n, nrhs, CUDA_C_64F, A, n, ls.ipiv.as<int64_t>(),
+    PWQT_SOLVER(c, cusolverDnXgetrs(wk.sol, wk.prm, CUBLAS_OP_N, n, nrhs, CUDA_C_64F, A, n, ls.ipiv.as<int64_t>(),
                                     CUDA_C_64F, B, n, ls.info.as<int>()));
     return PWQT_OK;
 }
 }  // namespace
 
-int lead_entry(pwqt_ctx* c, double Ec, LeadEntry** out) {
-    auto it = c->cache.find(Ec);
-    if (it != c->cache.end()) { *out = it->second.get(); return PWQT_OK; }
-    const int n = c->n, n2 = 2 * n;
-    const double L = c->Lz;
-    cudaStream_t st = c->stream;
+// bz: the context that owns the basis (read only); c: a private context for errors.
+int compute_lead_shared(const pwqt_ctx* bz, pwqt_ctx* c, const LeadWorker& wk, double Ec,
+                        std::unique_ptr<LeadEntry>& result) {
+    const int n = bz->n, n2 = 2 * n;
+    const double L = bz->Lz;
+    cudaStream_t st = wk.stream;
     const dim3 b128(128);
+    long long launches = 0;
     DBuf K0, Kp, ApB, AmB, Wmu, VR, lam, Cm, Q, Mk, x, y, forms;
     PWQT_TRY(alloc(c, K0, sizeof(double2) * n * n));
     PWQT_TRY(alloc(c, Kp, sizeof(double2) * n * n));
     PWQT_TRY(alloc(c, ApB, sizeof(double2) * (size_t)n2 * n2));
     PWQT_TRY(alloc(c, AmB, sizeof(double2) * (size_t)n2 * n2));
-    k_lead_K<<<dim3((n + 127) / 128, n), b128, 0, st>>>(n, Ec, c->H0.as<double2>(), c->H1.as<double2>(), c->M0.as<double2>(),
-                                                      c->M1.as<double2>(), K0.as<double2>(), Kp.as<double2>());
+    k_lead_K<<<dim3((n + 127) / 128, n), b128, 0, st>>>(n, Ec, bz->H0.as<double2>(), bz->H1.as<double2>(), bz->M0.as<double2>(),
+                                                      bz->M1.as<double2>(), K0.as<double2>(), Kp.as<double2>());
     k_lead_cayley<<<dim3((n2 + 127) / 128, n2), b128, 0, st>>>(n, K0.as<double2>(), Kp.as<double2>(), ApB.as<double2>(),
                                                              AmB.as<double2>());
-    c->launches += 2;
+    launches += 2;
     PWQT_CUDA(c, cudaGetLastError());
     LinSolve ls;
-    PWQT_TRY(lu_solve(c, ls, n2, ApB.as<double2>(), AmB.as<double2>(), n2));   // AmB <- (A+B)^-1 (A-B)
+    PWQT_TRY(lu_solve(c, wk, ls, n2, ApB.as<double2>(), AmB.as<double2>(), n2));   // AmB <- (A+B)^-1 (A-B)
     // eigen-decomposition of the Cayley-transformed pencil
     PWQT_TRY(alloc(c, Wmu, sizeof(double2) * n2));
     PWQT_TRY(alloc(c, VR, sizeof(double2) * (size_t)n2 * n2));
     size_t wd = 0, wh = 0;
-    PWQT_SOLVER(c, cusolverDnXgeev_bufferSize(c->sol, c->prm, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR, n2, CUDA_C_64F,
+    PWQT_SOLVER(c, cusolverDnXgeev_bufferSize(wk.sol, wk.prm, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR, n2, CUDA_C_64F,
                                               AmB.p, n2, CUDA_C_64F, Wmu.p, CUDA_C_64F, nullptr, n2, CUDA_C_64F, VR.p, n2,
                                               CUDA_C_64F, &wd, &wh));
     DBuf gw;
     PWQT_TRY(alloc(c, gw, std::max<size_t>(wd, 16)));
     std::vector<char> gh(wh + 16);
-    PWQT_SOLVER(c, cusolverDnXgeev(c->sol, c->prm, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR, n2, CUDA_C_64F, AmB.p, n2,
+    PWQT_SOLVER(c, cusolverDnXgeev(wk.sol, wk.prm, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR, n2, CUDA_C_64F, AmB.p, n2,
                                    CUDA_C_64F, Wmu.p, CUDA_C_64F, nullptr, n2, CUDA_C_64F, VR.p, n2, CUDA_C_64F, gw.p, wd,
                                    gh.data(), wh, ls.info.as<int>()));
     int hinfo = 0;
@@ -257,7 +260,7 @@ int lead_entry(pwqt_ctx* c, double Ec, LeadEntry** out) {
     PWQT_TRY(alloc(c, lam, sizeof(double2) * n2));
     PWQT_TRY(alloc(c, Cm, sizeof(double2) * (size_t)n * n2));
     k_lead_modes<<<n2, 256, 0, st>>>(n, Wmu.as<double2>(), VR.as<double2>(), lam.as<double2>(), Cm.as<double2>());
-    c->launches++;
+    launches++;
     PWQT_CUDA(c, cudaGetLastError());
     std::vector<double2> hlam(n2);
     PWQT_CUDA(c, cudaMemcpyAsync(hlam.data(), lam.p, sizeof(double2) * n2, cudaMemcpyDeviceToHost, st));
@@ -277,8 +280,8 @@ int lead_entry(pwqt_ctx* c, double Ec, LeadEntry** out) {
     const double tol_E = 1e-13 * std::max(1.0, std::fabs(Ec));
     for (int j = 0; j < n2; ++j) {
         double al = std::hypot(hlam[j].x, hlam[j].y);
-        if (std::fabs(al - 1.0) >= 1e-6) {
-            if (std::fabs(al - 1.0) < 1e-5) status |= PWQT_ST_NEAR_UNIT;
+        if (std::fabs(al - 1.0) >= 1e-4) {
+            if (std::fabs(al - 1.0) < 1e-3) status |= PWQT_ST_NEAR_UNIT;
             continue;
         }
         trav[j] = 1;
@@ -288,16 +291,16 @@ int lead_entry(pwqt_ctx* c, double Ec, LeadEntry** out) {
         double2 ph = make_double2(std::cos(k * L), std::sin(k * L));
         for (int iter = 0; iter < 8; ++iter) {
             ph = make_double2(std::cos(k * L), std::sin(k * L));
-            k_lead_hk<<<dim3((n + 127) / 128, n), b128, 0, st>>>(n, ph, Ec, c->H0.as<double2>(), c->H1.as<double2>(),
-                                                               c->M0.as<double2>(), c->M1.as<double2>(), Q.as<double2>(),
+            k_lead_hk<<<dim3((n + 127) / 128, n), b128, 0, st>>>(n, ph, Ec, bz->H0.as<double2>(), bz->H1.as<double2>(),
+                                                               bz->M0.as<double2>(), bz->M1.as<double2>(), Q.as<double2>(),
                                                                Mk.as<double2>());
             k_matvec_cm<<<(n + 127) / 128, b128, 0, st>>>(n, Mk.as<double2>(), x.as<double2>(), y.as<double2>());
-            c->launches += 2;
-            PWQT_TRY(lu_solve(c, ls, n, Q.as<double2>(), y.as<double2>(), 1));   // y <- (H(k) - Ec M(k))^-1 M(k) x
+            launches += 2;
+            PWQT_TRY(lu_solve(c, wk, ls, n, Q.as<double2>(), y.as<double2>(), 1));   // y <- (H(k) - Ec M(k))^-1 M(k) x
             PWQT_CUDA(c, cudaMemcpyAsync(x.p, y.p, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
-            k_lead_forms<<<1, 256, 0, st>>>(n, ph, L, c->H0.as<double2>(), c->H1.as<double2>(), c->M0.as<double2>(),
-                                            c->M1.as<double2>(), x.as<double2>(), forms.as<double>());
-            c->launches++;
+            k_lead_forms<<<1, 256, 0, st>>>(n, ph, L, bz->H0.as<double2>(), bz->H1.as<double2>(), bz->M0.as<double2>(),
+                                            bz->M1.as<double2>(), x.as<double2>(), forms.as<double>());
+            launches++;
             PWQT_CUDA(c, cudaMemcpyAsync(hf, forms.p, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
             PWQT_CUDA(c, cudaStreamSynchronize(st));
             double w = hf[0], slope = hf[2];
@@ -310,7 +313,7 @@ int lead_entry(pwqt_ctx* c, double Ec, LeadEntry** out) {
         double scale = std::sqrt(L / (2.0 * M_PI) / hf[1]);
         PWQT_CUDA(c, cudaMemcpyAsync(Cm.as<double2>() + (size_t)j * n, x.p, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
         k_scale_col<<<(n + 127) / 128, b128, 0, st>>>(Cm.as<double2>(), n, j, scale);
-        c->launches++;
+        launches++;
     }
     // degenerate traveling modes (same lambda) are not flux-orthogonalised here: flag them
     for (int a = 0; a < n2; ++a)
@@ -331,8 +334,8 @@ int lead_entry(pwqt_ctx* c, double Ec, LeadEntry** out) {
     E->Ec = Ec;
     if ((int)out_d.size() != n || (int)out_s.size() != n) {
         E->status = status | PWQT_ST_MODE_COUNT;
-        c->cache[Ec] = std::move(E);
-        *out = c->cache[Ec].get();
+        E->launches = launches;
+        result = std::move(E);
         return PWQT_OK;
     }
     // ---- self-energies, projections and injection vectors for both contacts
@@ -369,17 +372,17 @@ int lead_entry(pwqt_ctx* c, double Ec, LeadEntry** out) {
         k_gather_cols<<<dim3((n + 127) / 128, n), b128, 0, st>>>(n, Cm.as<double2>(), didx.as<int>(), nullptr, B.as<double2>());
         k_gather_cols<<<dim3((n + 127) / 128, n), b128, 0, st>>>(n, Cm.as<double2>(), didx.as<int>(), dlam.as<double2>(), BL.as<double2>());
         k_identity<<<dim3((n + 127) / 128, n), b128, 0, st>>>(n, Binv.as<double2>());
-        c->launches += 3;
-        PWQT_TRY(lu_solve(c, ls, n, B.as<double2>(), Binv.as<double2>(), n));   // Binv = B^-1
+        launches += 3;
+        PWQT_TRY(lu_solve(c, wk, ls, n, B.as<double2>(), Binv.as<double2>(), n));   // Binv = B^-1
         cuDoubleComplex one = {1, 0}, zero = {0, 0}, mone = {-1, 0};
         // T1 = (B Lambda) B^-1 ; Sigma = K' T1   (K'_d = K+, K'_s = K- = K+^H), column-major
-        PWQT_BLAS(c, cublasZgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, BL.as<cuDoubleComplex>(), n,
+        PWQT_BLAS(c, cublasZgemm(wk.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, BL.as<cuDoubleComplex>(), n,
                                  Binv.as<cuDoubleComplex>(), n, &zero, T1.as<cuDoubleComplex>(), n));
-        PWQT_BLAS(c, cublasZgemm(c->blas, drain ? CUBLAS_OP_N : CUBLAS_OP_C, CUBLAS_OP_N, n, n, n, &one, Kp.as<cuDoubleComplex>(), n,
+        PWQT_BLAS(c, cublasZgemm(wk.blas, drain ? CUBLAS_OP_N : CUBLAS_OP_C, CUBLAS_OP_N, n, n, n, &one, Kp.as<cuDoubleComplex>(), n,
                                  T1.as<cuDoubleComplex>(), n, &zero, S.as<cuDoubleComplex>(), n));
         PWQT_TRY(alloc(c, sigma, sizeof(double2) * n * n));
         transpose_c128(S.as<double2>(), sigma.as<double2>(), n, n, st);   // column-major -> row-major
-        c->launches++;
+        launches++;
         // rows of B^-1 for traveling out-flow modes
         PWQT_TRY(alloc(c, P, sizeof(double2) * (size_t)std::max(ntrav, 1) * n));
         PWQT_TRY(alloc(c, vout, sizeof(double) * std::max(ntrav, 1)));
@@ -387,7 +390,7 @@ int lead_entry(pwqt_ctx* c, double Ec, LeadEntry** out) {
             PWQT_TRY(alloc(c, dtr, sizeof(int) * ntrav));
             PWQT_CUDA(c, cudaMemcpyAsync(dtr.p, trows.data(), sizeof(int) * ntrav, cudaMemcpyHostToDevice, st));
             k_gather_rows<<<dim3((n + 127) / 128, ntrav), b128, 0, st>>>(n, Binv.as<double2>(), dtr.as<int>(), P.as<double2>());
-            c->launches++;
+            launches++;
             PWQT_CUDA(c, cudaMemcpyAsync(vout.p, tv.data(), sizeof(double) * ntrav, cudaMemcpyHostToDevice, st));
         }
         // injection vectors rhs = K' C_in Lambda_in - Sigma C_in  (n x m), stored row-major
@@ -410,20 +413,20 @@ int lead_entry(pwqt_ctx* c, double Ec, LeadEntry** out) {
             PWQT_TRY(alloc(c, CinL, sizeof(double2) * (size_t)n * m));
             k_gather_cols<<<dim3((n + 127) / 128, m), b128, 0, st>>>(n, Cm.as<double2>(), didx2.as<int>(), nullptr, Cin.as<double2>());
             k_gather_cols<<<dim3((n + 127) / 128, m), b128, 0, st>>>(n, Cm.as<double2>(), didx2.as<int>(), dli.as<double2>(), CinL.as<double2>());
-            c->launches += 2;
+            launches += 2;
             // R1 = K' (C_in Lambda) - Sigma C_in
-            PWQT_BLAS(c, cublasZgemm(c->blas, drain ? CUBLAS_OP_N : CUBLAS_OP_C, CUBLAS_OP_N, n, m, n, &one,
+            PWQT_BLAS(c, cublasZgemm(wk.blas, drain ? CUBLAS_OP_N : CUBLAS_OP_C, CUBLAS_OP_N, n, m, n, &one,
                                      Kp.as<cuDoubleComplex>(), n, CinL.as<cuDoubleComplex>(), n, &zero, R1.as<cuDoubleComplex>(), n));
-            PWQT_BLAS(c, cublasZgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, m, n, &mone, S.as<cuDoubleComplex>(), n,
+            PWQT_BLAS(c, cublasZgemm(wk.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, m, n, &mone, S.as<cuDoubleComplex>(), n,
                                      Cin.as<cuDoubleComplex>(), n, &one, R1.as<cuDoubleComplex>(), n));
             transpose_c128(R1.as<double2>(), rhs.as<double2>(), m, n, st);   // (n x m col-major) -> row-major n x m
             if (cin) transpose_c128(Cin.as<double2>(), cin->as<double2>(), m, n, st);
-            c->launches += 2;
+            launches += 2;
         }
         PWQT_CUDA(c, cudaStreamSynchronize(st));
         return PWQT_OK;
     };
-    PWQT_BLAS(c, cublasSetStream(c->blas, st));
+    
     PWQT_TRY(build(true, E->sigma_d, E->P_d, E->v_out_d, E->rhs_d, E->v_in_d, nullptr, E->n_trav_out_d, E->m_in_d));
     PWQT_TRY(build(false, E->sigma_s, E->P_s, E->v_out_s, E->rhs_s, E->v_in_s, &E->cin_s, E->n_trav_out_s, E->m_in_s));
     size_t nn = (size_t)n * n;
@@ -435,11 +438,82 @@ int lead_entry(pwqt_ctx* c, double Ec, LeadEntry** out) {
     c128_to_c64(E->sigma_s.as<double2>(), E->sigma_s32.as<float2>(), nn, st);
     c128_to_c64(E->rhs_d.as<double2>(), E->rhs_d32.as<float2>(), (size_t)n * E->m_in_d, st);
     c128_to_c64(E->rhs_s.as<double2>(), E->rhs_s32.as<float2>(), (size_t)n * E->m_in_s, st);
-    c->launches += 4;
+    launches += 4;
     PWQT_CUDA(c, cudaStreamSynchronize(st));
     E->status = status;
-    c->cache[Ec] = std::move(E);
-    *out = c->cache[Ec].get();
+    E->launches = launches;
+    result = std::move(E);
+    return PWQT_OK;
+}
+
+int LeadWorker::init() {
+    if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) return PWQT_ERR_CUDA;
+    if (cusolverDnCreate(&sol) != CUSOLVER_STATUS_SUCCESS || cusolverDnCreateParams(&prm) != CUSOLVER_STATUS_SUCCESS ||
+        cublasCreate(&blas) != CUBLAS_STATUS_SUCCESS)
+        return PWQT_ERR_CUDA;
+    cusolverDnSetStream(sol, stream);
+    cublasSetStream(blas, stream);
+    return PWQT_OK;
+}
+void LeadWorker::destroy() {
+    if (prm) cusolverDnDestroyParams(prm);
+    if (sol) cusolverDnDestroy(sol);
+    if (blas) cublasDestroy(blas);
+    if (stream) cudaStreamDestroy(stream);
+    prm = nullptr; sol = nullptr; blas = nullptr; stream = nullptr;
+}
+
+// Fill the cache for every key in `keys` that is missing, with up to
+// opts-independent min(#missing, 8) host threads, each driving its own stream and
+// solver handles (the eigensolver is latency-bound; concurrent energies overlap).
+int fill_leads(pwqt_ctx* c, const std::vector<double>& keys) {
+    std::vector<double> miss;
+    for (double k : keys)
+        if (!c->cache.count(k) && std::find(miss.begin(), miss.end(), k) == miss.end()) miss.push_back(k);
+    if (miss.empty()) return PWQT_OK;
+    int nthreads = (int)std::min<size_t>(miss.size(), (size_t)std::max(1, c->lead_threads));
+    while ((int)c->workers.size() < nthreads) {
+        c->workers.emplace_back(new LeadWorker());
+        int r = c->workers.back()->init();
+        if (r != PWQT_OK) { c->workers.back()->destroy(); c->workers.pop_back(); if (c->workers.empty()) return fail(c, r, "lead worker init"); break; }
+    }
+    nthreads = std::min<int>(nthreads, (int)c->workers.size());
+    std::vector<std::unique_ptr<LeadEntry>> res(miss.size());
+    std::vector<int> rc(nthreads, PWQT_OK);
+    std::vector<std::string> errs(nthreads);
+    std::atomic<size_t> next{0};
+    auto work = [&](int t) {
+        cudaSetDevice(c->dev);
+        pwqt_ctx local;      // private error slot; the worker owns stream and handles
+        local.dev = c->dev;
+        local.n = c->n; local.Lz = c->Lz;
+        for (;;) {
+            size_t i = next.fetch_add(1);
+            if (i >= miss.size()) break;
+            int r = compute_lead_shared(c, &local, *c->workers[t], miss[i], res[i]);
+            if (r != PWQT_OK) { rc[t] = r; errs[t] = local.err; break; }
+        }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nthreads; ++t) th.emplace_back(work, t);
+    work(0);
+    for (auto& x : th) x.join();
+    for (int t = 0; t < nthreads; ++t)
+        if (rc[t] != PWQT_OK) return fail(c, rc[t], errs[t]);
+    for (size_t i = 0; i < miss.size(); ++i) {
+        c->launches += res[i]->launches;
+        c->cache[miss[i]] = std::move(res[i]);
+    }
+    return PWQT_OK;
+}
+
+int lead_entry(pwqt_ctx* c, double Ec, LeadEntry** out) {
+    auto it = c->cache.find(Ec);
+    if (it == c->cache.end()) {
+        PWQT_TRY(fill_leads(c, std::vector<double>{Ec}));
+        it = c->cache.find(Ec);
+    }
+    *out = it->second.get();
     return PWQT_OK;
 }
 

@@ -66,10 +66,14 @@ int pwqt_destroy(pwqt_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     c->cache.clear();
     c->systems.clear();
+    for (auto& w : c->workers) w->destroy();
+    c->workers.clear();
     if (c->prm) cusolverDnDestroyParams(c->prm);
     if (c->sol) cusolverDnDestroy(c->sol);
     if (c->blas) cublasDestroy(c->blas);
     if (c->stream) cudaStreamDestroy(c->stream);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
     delete c;
     return PWQT_OK;
 }
@@ -198,12 +202,9 @@ int pwqt_prepare_leads(pwqt_ctx* c, int sys, int n_E, const double* E) {
     if (it == c->systems.end()) return fail(c, PWQT_ERR_STATE, "unknown system");
     if (n_E < 0 || (n_E && !E)) return fail(c, PWQT_ERR_INVALID_ARG, "bad energies");
     cudaSetDevice(c->dev);
-    for (int e = 0; e < n_E; ++e) {
-        LeadEntry* le;
-        PWQT_TRY(lead_entry(c, E[e] - it->second.Us, &le));
-        PWQT_TRY(lead_entry(c, E[e] - it->second.Ud, &le));
-    }
-    return PWQT_OK;
+    std::vector<double> keys;
+    for (int e = 0; e < n_E; ++e) { keys.push_back(E[e] - it->second.Us); keys.push_back(E[e] - it->second.Ud); }
+    return fill_leads(c, keys);
 }
 
 int pwqt_cache_info(pwqt_ctx* c, int* entries, size_t* bytes) {
@@ -242,6 +243,21 @@ int pwqt_bands(pwqt_ctx* c, int n_k, const double* k, double* E_out) {
         PWQT_CUDA(c, cudaMemcpyAsync(E_out + (size_t)q * n, W.p, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
     }
     PWQT_CUDA(c, cudaStreamSynchronize(c->stream));
+    return PWQT_OK;
+}
+
+int pwqt_profile(pwqt_ctx* c, int enable, double* sweep_ms, long long* sweep_launches, double* sweep_flops, int reset) {
+    PWQT_TRY(check_ctx(c));
+    cudaSetDevice(c->dev);
+    if (enable && !c->ev0) {
+        PWQT_CUDA(c, cudaEventCreate(&c->ev0));
+        PWQT_CUDA(c, cudaEventCreate(&c->ev1));
+    }
+    c->profile = enable;
+    if (sweep_ms) *sweep_ms = c->prof_ms;
+    if (sweep_launches) *sweep_launches = c->prof_launches;
+    if (sweep_flops) *sweep_flops = c->prof_flops;
+    if (reset) { c->prof_ms = 0; c->prof_launches = 0; c->prof_flops = 0; }
     return PWQT_OK;
 }
 

@@ -75,7 +75,18 @@ struct LeadEntry {
     DBuf cin_s;                                // n x m_s injected source modes (for R)
     DBuf v_in_d, v_in_s;                       // |dE/dk| of injected modes
     DBuf sigma_d32, sigma_s32, rhs_d32, rhs_s32;   // complex64 copies (mixed path)
+    long long launches = 0;                    // kernels launched to build this entry
     size_t bytes() const;
+};
+
+// Stream and library handles of one host thread that fills the contact cache.
+struct LeadWorker {
+    cudaStream_t stream = nullptr;
+    cusolverDnHandle_t sol = nullptr;
+    cusolverDnParams_t prm = nullptr;
+    cublasHandle_t blas = nullptr;
+    int init();
+    void destroy();
 };
 
 struct System {
@@ -108,6 +119,20 @@ struct pwqt_ctx {
     std::map<double, std::unique_ptr<pwqt::LeadEntry>> cache;
     // scratch reused across calls
     pwqt::DBuf work_a, work_b;
+    // grow-only workspaces of the sweep (kept across calls: no allocation in steady state)
+    pwqt::DBuf ws_xy, ws_s, ws_norms, ws_jobs, ws_obs, ws_res, ws_mixed;
+    // optional CUDA-event timing of the dominant (block-sweep) kernels
+    int profile = 0;
+    double prof_ms = 0.0;
+    long long prof_launches = 0;
+    double prof_flops = 0.0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // host threads that fill the contact cache concurrently
+    int lead_threads = 8;
+    std::vector<std::unique_ptr<pwqt::LeadWorker>> workers;
+    ~pwqt_ctx() {
+        for (auto& w : workers) w->destroy();
+    }
 };
 
 namespace pwqt {
@@ -121,6 +146,7 @@ int cuda_fail(pwqt_ctx* c, cudaError_t e, const char* what);
 #define PWQT_TRY(x) do { int r_ = (x); if (r_ != PWQT_OK) return r_; } while (0)
 
 int alloc(pwqt_ctx* c, DBuf& b, size_t bytes);
+int ensure(pwqt_ctx* c, DBuf& b, size_t bytes);   // grow-only
 
 // assembly (assemble.cu)
 int assemble_from_basis(pwqt_ctx* c, const pwqt_cell* cell, int n_bands, const double* eps_host,
@@ -130,6 +156,7 @@ int build_system_blocks(pwqt_ctx* c, System& s);
 
 // leads (lead.cu)
 int lead_entry(pwqt_ctx* c, double Ec, LeadEntry** out);
+int fill_leads(pwqt_ctx* c, const std::vector<double>& keys);
 
 // solve (solve.cu)
 struct SolveOut {

@@ -140,6 +140,11 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
     const size_t nn = (size_t)n * n;
     // 1. contact data (FP64 cache, computed on a miss)
     std::vector<LeadEntry*> ls(nE), ld(nE);
+    {
+        std::vector<double> keys;
+        for (int e = 0; e < nE; ++e) { keys.push_back(E[e] - s.Us); keys.push_back(E[e] - s.Ud); }
+        PWQT_TRY(fill_leads(c, keys));
+    }
     for (int e = 0; e < nE; ++e) {
         PWQT_TRY(lead_entry(c, E[e] - s.Us, &ls[e]));
         PWQT_TRY(lead_entry(c, E[e] - s.Ud, &ld[e]));
@@ -180,11 +185,11 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
         for (int b = 0; b < nb; ++b) off[b + 1] = off[b] + (size_t)N * n * (n + ms[e0 + b] + md[e0 + b]);
         size_t maxm = 1;
         for (int b = 0; b < nb; ++b) maxm = std::max<size_t>(maxm, ms[e0 + b] + md[e0 + b]);
-        DBuf XY, Sb, jobs_d, obs_d, res_d, norms;
-        PWQT_TRY(alloc(c, XY, sizeof(double2) * std::max<size_t>(off[nb], 1)));
-        PWQT_TRY(alloc(c, Sb, sizeof(double2) * nn * nb));
-        PWQT_TRY(alloc(c, norms, sizeof(double) * 2 * nb * maxm));
-        PWQT_CUDA(c, cudaMemsetAsync(norms.p, 0, norms.bytes, st));
+        DBuf &XY = c->ws_xy, &Sb = c->ws_s, &jobs_d = c->ws_jobs, &obs_d = c->ws_obs, &res_d = c->ws_res, &norms = c->ws_norms;
+        PWQT_TRY(ensure(c, XY, sizeof(double2) * std::max<size_t>(off[nb], 1)));
+        PWQT_TRY(ensure(c, Sb, sizeof(double2) * nn * nb));
+        PWQT_TRY(ensure(c, norms, sizeof(double) * 2 * nb * maxm));
+        PWQT_CUDA(c, cudaMemsetAsync(norms.p, 0, sizeof(double) * 2 * nb * maxm, st));
         std::vector<SweepJob> jobs(nb);
         std::vector<ObsJob> obs(nb);
         std::vector<ResJob> res(nb);
@@ -227,17 +232,27 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
         // statuses from the contacts
         for (int b = 0; b < nb; ++b)
             PWQT_CUDA(c, cudaMemcpyAsync(o.status + e0 + b, &hst[e0 + b], sizeof(int), cudaMemcpyHostToDevice, st));
-        PWQT_TRY(alloc(c, jobs_d, sizeof(SweepJob) * nb));
-        PWQT_TRY(alloc(c, obs_d, sizeof(ObsJob) * nb));
-        PWQT_TRY(alloc(c, res_d, sizeof(ResJob) * nb));
+        PWQT_TRY(ensure(c, jobs_d, sizeof(SweepJob) * nb));
+        PWQT_TRY(ensure(c, obs_d, sizeof(ObsJob) * nb));
+        PWQT_TRY(ensure(c, res_d, sizeof(ResJob) * nb));
         PWQT_CUDA(c, cudaMemcpyAsync(jobs_d.p, jobs.data(), sizeof(SweepJob) * nb, cudaMemcpyHostToDevice, st));
         PWQT_CUDA(c, cudaMemcpyAsync(obs_d.p, obs.data(), sizeof(ObsJob) * nb, cudaMemcpyHostToDevice, st));
         PWQT_CUDA(c, cudaMemcpyAsync(res_d.p, res.data(), sizeof(ResJob) * nb, cudaMemcpyHostToDevice, st));
         if (precision == PWQT_MIXED) {
             PWQT_TRY(solve_mixed(c, s, sys, jobs, jobs_d.as<SweepJob>(), res, res_d.as<ResJob>(), nb, o.iters + e0, st));
         } else {
+            if (c->profile) PWQT_CUDA(c, cudaEventRecord(c->ev0, st));
             launch_sweep_fp64(sys, jobs_d.as<SweepJob>(), nb, st);
             c->launches++;
+            if (c->profile) {
+                PWQT_CUDA(c, cudaEventRecord(c->ev1, st));
+                PWQT_CUDA(c, cudaEventSynchronize(c->ev1));
+                float ms = 0;
+                cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+                c->prof_ms += ms;
+                c->prof_launches += 1;
+                c->prof_flops += (56.0 / 3.0) * (double)N * n * n * (double)n * nb;
+            }
             PWQT_CUDA(c, cudaGetLastError());
             launch_residual_fp64(sys, res_d.as<ResJob>(), nb, st);
             c->launches += 2;

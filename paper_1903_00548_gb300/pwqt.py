@@ -22,7 +22,7 @@ ST_SINGULAR_PIVOT, ST_MODE_COUNT, ST_IR_NO_CONVERGE, ST_DEGENERATE, ST_NEAR_UNIT
 
 EXPORTS = ["pwqt_create", "pwqt_destroy", "pwqt_last_error", "pwqt_assemble_intrinsic", "pwqt_set_enhancement",
            "pwqt_get_blocks", "pwqt_set_extrinsic", "pwqt_solve", "pwqt_solve_dev", "pwqt_prepare_leads",
-           "pwqt_cache_info", "pwqt_bands", "pwqt_kernel_launches"]
+           "pwqt_cache_info", "pwqt_bands", "pwqt_kernel_launches", "pwqt_profile"]
 
 
 class PwqtError(RuntimeError):
@@ -72,6 +72,7 @@ def load(path: str = LIB_PATH):
     lib.pwqt_cache_info.argtypes = [P, ip, C.POINTER(S)]
     lib.pwqt_bands.argtypes = [P, I, dp, dp]
     lib.pwqt_kernel_launches.argtypes = [P, C.POINTER(C.c_longlong), I]
+    lib.pwqt_profile.argtypes = [P, I, dp, C.POINTER(C.c_longlong), dp, I]
     for f in EXPORTS:
         if f != "pwqt_last_error":
             getattr(lib, f).restype = C.c_int
@@ -206,6 +207,12 @@ class Context:
         out = np.zeros((len(k), self.n))
         self._check(self.lib.pwqt_bands(self.h, len(k), _dptr(k), _dptr(out)))
         return out
+
+    def profile(self, enable: bool = True, reset: bool = False):
+        ms, cnt, fl = C.c_double(), C.c_longlong(), C.c_double()
+        self._check(self.lib.pwqt_profile(self.h, 1 if enable else 0, C.byref(ms), C.byref(cnt), C.byref(fl),
+                                          1 if reset else 0))
+        return ms.value, cnt.value, fl.value
 
     def kernel_launches(self, reset: bool = False) -> int:
         v = C.c_longlong()
