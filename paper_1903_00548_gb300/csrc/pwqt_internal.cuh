@@ -121,6 +121,7 @@ struct pwqt_ctx {
     pwqt::DBuf work_a, work_b;
     // grow-only workspaces of the sweep (kept across calls: no allocation in steady state)
     pwqt::DBuf ws_xy, ws_s, ws_norms, ws_jobs, ws_obs, ws_res, ws_mixed;
+    pwqt::DBuf zero_nn;   // n x n zeros
     // optional CUDA-event timing of the dominant (block-sweep) kernels
     int profile = 0;
     double prof_ms = 0.0;

@@ -167,6 +167,13 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
         return b;
     };
     SweepSys sys{n, N, c->M0.as<double2>(), c->M1.as<double2>(), s.HV0.as<double2>(), s.HV1.as<double2>()};
+    // energies whose contacts failed the mode count get zero self-energies and no
+    // injected modes (their status carries PWQT_ST_MODE_COUNT)
+    if (c->zero_nn.bytes < sizeof(double2) * nn) {
+        PWQT_TRY(alloc(c, c->zero_nn, sizeof(double2) * nn));
+        PWQT_CUDA(c, cudaMemset(c->zero_nn.p, 0, c->zero_nn.bytes));
+    }
+    const double2* zero = c->zero_nn.as<double2>();
     PWQT_BLAS(c, cublasSetStream(c->blas, st));
     int e0 = 0;
     while (e0 < nE) {
@@ -201,10 +208,11 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
             J.E = E[e];
             J.ms = ms[e];
             J.md = md[e];
-            J.sig_s = Ls->sigma_s.as<double2>();
-            J.sig_d = Ld->sigma_d.as<double2>();
-            J.rhs_s = Ls->rhs_s.as<double2>();
-            J.rhs_d = Ld->rhs_d.as<double2>();
+            const bool bad = (hst[e] & PWQT_ST_MODE_COUNT) != 0;
+            J.sig_s = bad ? zero : Ls->sigma_s.as<double2>();
+            J.sig_d = bad ? zero : Ld->sigma_d.as<double2>();
+            J.rhs_s = bad ? zero : Ls->rhs_s.as<double2>();
+            J.rhs_d = bad ? zero : Ld->rhs_d.as<double2>();
             J.XY = XY.as<double2>() + off[b];
             J.S = Sb.as<double2>() + nn * b;
             J.status = o.status + e;
@@ -215,10 +223,10 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
             O.C = J.XY + n;
             O.node_stride = (size_t)n * (n + m);
             O.row_stride = n + m;
-            O.P_d = Ld->P_d.as<double2>(); O.P_s = Ls->P_s.as<double2>();
-            O.v_out_d = Ld->v_out_d.as<double>(); O.v_out_s = Ls->v_out_s.as<double>();
-            O.v_in_d = Ld->v_in_d.as<double>(); O.v_in_s = Ls->v_in_s.as<double>();
-            O.cin_s = Ls->cin_s.as<double2>();
+            O.P_d = bad ? nullptr : Ld->P_d.as<double2>(); O.P_s = bad ? nullptr : Ls->P_s.as<double2>();
+            O.v_out_d = bad ? nullptr : Ld->v_out_d.as<double>(); O.v_out_s = bad ? nullptr : Ls->v_out_s.as<double>();
+            O.v_in_d = bad ? nullptr : Ld->v_in_d.as<double>(); O.v_in_s = bad ? nullptr : Ls->v_in_s.as<double>();
+            O.cin_s = bad ? nullptr : Ls->cin_s.as<double2>();
             O.T = o.T + e; O.R = o.R + e; O.T_ds = o.T_ds + e; O.node_n = o.node_n + (size_t)e * N * 2;
             ResJob& Rj = res[b];
             Rj.E = E[e]; Rj.ms = ms[e]; Rj.md = md[e];

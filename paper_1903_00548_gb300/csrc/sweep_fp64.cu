@@ -96,8 +96,8 @@ __global__ void __launch_bounds__(NT) k_sweep_fp64(SweepSys sys, const SweepJob*
         const double2* HV1 = sys.HV1 + (size_t)i * n * n;
         for (int t = threadIdx.x; t < n * n; t += NT) {
             double2 v = csub(cscale(sys.M0[t], E), HV0[t]);
-            if (i == 0) v = csub(v, J.sig_s[t]);
-            if (i == N - 1) v = csub(v, J.sig_d[t]);
+            if (i == 0 && J.sig_s) v = csub(v, J.sig_s[t]);
+            if (i == N - 1 && J.sig_d) v = csub(v, J.sig_d[t]);
             S[t] = v;
         }
         for (int t = threadIdx.x; t < n * w; t += NT) {
