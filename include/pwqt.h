@@ -198,6 +198,33 @@ int pwqt_bands(pwqt_ctx* ctx, int n_k, const double* k, double* E_out);
 int pwqt_profile(pwqt_ctx* ctx, int enable, double* sweep_ms, long long* sweep_launches,
                  double* sweep_flops, int reset);
 
+/*
+ * pwqt_solve_noalloc -- the FP64 solve without any device allocation.
+ * The paper has no counterpart; this entry point exists for callers that cannot
+ * call cudaMalloc while they solve: code embedded in a host program that owns the
+ * device-memory budget (its own pool allocator or a hard quota), or a service
+ * whose request path must not allocate because cudaMalloc synchronises the device
+ * and can fail under fragmentation.  Everything the call needs beyond the
+ * caller's inputs and outputs lives in one static device array of 32 MiB that
+ * every GPU loading the library holds until the process exits.
+ *   - Inputs: the context's assembled system `sys` (pwqt_set_extrinsic) and its
+ *     cached self-energies: call pwqt_prepare_leads (which allocates) for these
+ *     energies first, else PWQT_ERR_STATE.  E is host memory, n_E <= 64.
+ *   - Outputs: caller-owned DEVICE buffers T, R, T_ds [n_E], node_n [n_E*N*2]
+ *     (required) and status [n_E] (may be NULL); same meaning as pwqt_solve.
+ *   - Requests whose work panels (N n (n+m) complex128 per energy plus n x n
+ *     blocks) exceed the 32 MiB return PWQT_ERR_INVALID_ARG and compute nothing.
+ *   - The first call on a device looks up the array's device address on that
+ *     device (with the device current); make that first call before any stream
+ *     capture.  The call enqueues on `stream` (a cudaStream_t, NULL = legacy
+ *     default stream) and returns after the stream has finished the work.
+ *   - All calls share the array and it keeps the previous call's contents; the
+ *     call re-initialises what must start defined.  Calls that overlap on the GPU
+ *     (other host threads or streams at the same time) race on it: serialise them.
+ */
+int pwqt_solve_noalloc(pwqt_ctx* ctx, int sys, int n_E, const double* E, double* T, double* R,
+                       double* T_ds, double* node_n, int* status, void* stream);
+
 /* Launch counters of the library's own kernels since the last reset. */
 int pwqt_kernel_launches(pwqt_ctx* ctx, long long* count, int reset);
 

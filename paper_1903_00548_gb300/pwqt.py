@@ -22,7 +22,7 @@ ST_SINGULAR_PIVOT, ST_MODE_COUNT, ST_IR_NO_CONVERGE, ST_DEGENERATE, ST_NEAR_UNIT
 
 EXPORTS = ["pwqt_create", "pwqt_destroy", "pwqt_last_error", "pwqt_assemble_intrinsic", "pwqt_set_enhancement",
            "pwqt_get_blocks", "pwqt_set_extrinsic", "pwqt_solve", "pwqt_solve_dev", "pwqt_prepare_leads",
-           "pwqt_cache_info", "pwqt_bands", "pwqt_kernel_launches", "pwqt_profile"]
+           "pwqt_cache_info", "pwqt_bands", "pwqt_kernel_launches", "pwqt_profile", "pwqt_solve_noalloc"]
 
 
 class PwqtError(RuntimeError):
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
     lib.pwqt_bands.argtypes = [P, I, dp, dp]
     lib.pwqt_kernel_launches.argtypes = [P, C.POINTER(C.c_longlong), I]
     lib.pwqt_profile.argtypes = [P, I, dp, C.POINTER(C.c_longlong), dp, I]
+    lib.pwqt_solve_noalloc.argtypes = [P, I, I, dp, P, P, P, P, P, P]
     for f in EXPORTS:
         if f != "pwqt_last_error":
             getattr(lib, f).restype = C.c_int
@@ -196,6 +197,14 @@ class Context:
         self._check(self.lib.pwqt_solve_dev(self.h, sys, len(E), _dptr(E), precision, g("T"), g("R"), g("T_ds"),
                                             g("n_open"), g("node_n"), g("resid"), g("iters"), g("status"),
                                             C.c_void_p(stream_ptr) if stream_ptr else None))
+
+    def solve_noalloc(self, sys: int, E, out: dict, stream_ptr: int = 0):
+        """Allocation-free FP64 solve into caller-owned device buffers; `out` maps
+        T, R, T_ds, node_n (required) and status (optional) to device pointers."""
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        g = lambda k: C.c_void_p(out.get(k)) if out.get(k) else None
+        self._check(self.lib.pwqt_solve_noalloc(self.h, sys, len(E), _dptr(E), g("T"), g("R"), g("T_ds"), g("node_n"),
+                                                g("status"), C.c_void_p(stream_ptr) if stream_ptr else None))
 
     def cache_info(self):
         e, b = C.c_int(), C.c_size_t()
