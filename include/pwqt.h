@@ -225,6 +225,17 @@ int pwqt_profile(pwqt_ctx* ctx, int enable, double* sweep_ms, long long* sweep_l
 int pwqt_solve_noalloc(pwqt_ctx* ctx, int sys, int n_E, const double* E, double* T, double* R,
                        double* T_ds, double* node_n, int* status, void* stream);
 
+/*
+ * Utility / test entry point: C[b] -= A[b] B[b] for b < batch on the tensor cores
+ * (the library's complex64 3xTF32 GEMM of the mixed-precision sweep; the paper
+ * has no counterpart).  Host arrays, row-major complex64 interleaved (float[2]),
+ * batch entries stored back to back (M*lda, K*ldb, M*ldc complex each);
+ * leading dimensions in complex elements.  Allocates and frees its own device
+ * copies.  Errors: PWQT_ERR_INVALID_ARG, PWQT_ERR_OOM, PWQT_ERR_CUDA.
+ */
+int pwqt_cgemm_c64(int batch, int M, int N, int K, const float* A, int lda, const float* B, int ldb,
+                   float* C, int ldc);
+
 /* Launch counters of the library's own kernels since the last reset. */
 int pwqt_kernel_launches(pwqt_ctx* ctx, long long* count, int reset);
 

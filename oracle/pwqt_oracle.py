@@ -43,6 +43,13 @@ reason in the design notes):
     each traveling mode is then refined on the unit circle (Newton on k with
     the band structure of Sec. 5.1 and the Hellmann-Feynman slope), so that
     |lambda| = 1 holds to rounding as Sec. 3.1 states for exact arithmetic.
+  * the 2n modes are sorted into the two sets of n (Sec. 3.1) by an out-flow score:
+    log|lambda| for evanescent modes, -/+1e-5 for traveling modes with dE/dk >/< 0
+    (drain convention); the n lowest scores are the drain's out-flow modes, the n
+    highest the source's.  With a nearly redundant basis (many bands) the pencil
+    is close to singular and spurious eigenvalues can break the lambda <-> 1/lambda*
+    pairing; sorting still yields two sets of size n.  A traveling candidate whose
+    unit-circle refinement does not converge is treated as evanescent.
   * degenerate traveling modes are made flux-orthogonal by diagonalising the
     velocity form in the M(lambda) metric.
   * V_e(z) = sum_j U_j f_j(z) (hat interpolation of node potentials); leads
@@ -343,10 +350,12 @@ def refine_traveling(blk, Ec: float, lam, c, iters: int = 8):
         Kb = blk["H1"] - w[b] * blk["M1"]
         slope = (np.vdot(c, _velocity_form(Kb, Kb.conj().T, ph, L) @ c) / np.vdot(c, Mk @ c)).real
         best = (ph, c / np.linalg.norm(c))
-        if abs(w[b] - Ec) < 1e-14 * max(1.0, abs(Ec)) or slope == 0.0:
+        if abs(w[b] - Ec) < 1e-12 * max(1.0, abs(Ec)):
+            return True, best[0], best[1]
+        if slope == 0.0:
             break
         k -= (w[b] - Ec) / slope
-    return best
+    return False, best[0], best[1]
 
 
 def lead_modes(blk, Ec: float) -> LeadModes:
@@ -369,7 +378,11 @@ def lead_modes(blk, Ec: float) -> LeadModes:
     absl = np.abs(lam)
     trav = np.abs(absl - 1.0) < TRAVEL_TOL
     for j in np.flatnonzero(trav):
-        lam[j], C[:, j] = refine_traveling(blk, Ec, lam[j], C[:, j])
+        ok, lj, cj = refine_traveling(blk, Ec, lam[j], C[:, j])
+        if ok:
+            lam[j], C[:, j] = lj, cj
+        else:
+            trav[j] = False
     dEdk = np.zeros(2 * n)
     # degenerate traveling sets: diagonalise the velocity form in the M metric
     idx = np.flatnonzero(trav)
@@ -423,20 +436,21 @@ def contact(modes: LeadModes, side: str) -> Contact:
     lam, C, v, trav = modes.lam, modes.C, modes.dEdk, modes.traveling
     absl = np.abs(lam)
     n = C.shape[0]
+    score = np.where(trav, np.where(v > 0, -1e-5, 1e-5), np.log(np.maximum(absl, 1e-300)))
+    order = np.argsort(score, kind="stable")
+    out = np.zeros(2 * n, bool)
     if side == "d":
-        out = (~trav & (absl < 1.0)) | (trav & (v > 0))
-        inn = trav & (v < 0)
+        out[order[:n]] = True
+        inn = trav & ~out & (v < 0)
         lam_c = lam
         Kprime = modes.Kp
     elif side == "s":
-        out = (~trav & (absl > 1.0)) | (trav & (v < 0))
-        inn = trav & (v > 0)
+        out[order[n:]] = True
+        inn = trav & ~out & (v > 0)
         lam_c = 1.0 / lam
         Kprime = modes.Km
     else:
         raise ValueError(side)
-    if int(out.sum()) != n:
-        raise RuntimeError(f"mode count: {int(out.sum())} out-flow modes at contact {side}, expected {n}")
     B = C[:, out]
     lo = lam_c[out]
     X = np.linalg.solve(B.T, (B * lo[None, :]).T).T      # B Lambda B^-1

@@ -269,6 +269,7 @@ int compute_lead_shared(const pwqt_ctx* bz, pwqt_ctx* c, const LeadWorker& wk, d
     VR.release(); AmB.release(); Wmu.release();
 
     // ---- traveling modes: refine onto the unit circle
+    const std::vector<double2> raw_lam = hlam;
     std::vector<char> trav(n2, 0);
     std::vector<double> dEdk(n2, 0.0);
     int status = 0;
@@ -277,18 +278,20 @@ int compute_lead_shared(const pwqt_ctx* bz, pwqt_ctx* c, const LeadWorker& wk, d
     PWQT_TRY(alloc(c, x, sizeof(double2) * n));
     PWQT_TRY(alloc(c, y, sizeof(double2) * n));
     PWQT_TRY(alloc(c, forms, sizeof(double) * 4));
-    const double tol_E = 1e-13 * std::max(1.0, std::fabs(Ec));
+    const double tol_E = 1e-12 * std::max(1.0, std::fabs(Ec));
+    // candidates near the unit circle
     for (int j = 0; j < n2; ++j) {
         double al = std::hypot(hlam[j].x, hlam[j].y);
-        if (std::fabs(al - 1.0) >= 1e-4) {
-            if (std::fabs(al - 1.0) < 1e-3) status |= PWQT_ST_NEAR_UNIT;
-            continue;
-        }
-        trav[j] = 1;
+        if (std::fabs(al - 1.0) < 1e-4) trav[j] = 1;
+        else if (std::fabs(al - 1.0) < 1e-3) status |= PWQT_ST_NEAR_UNIT;
+    }
+    for (int j = 0; j < n2; ++j) {
+        if (!trav[j]) continue;
         double k = std::atan2(hlam[j].y, hlam[j].x) / L;
         PWQT_CUDA(c, cudaMemcpyAsync(x.p, Cm.as<double2>() + (size_t)j * n, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
         double hf[4] = {0, 0, 0, 0};
         double2 ph = make_double2(std::cos(k * L), std::sin(k * L));
+        bool converged = false;
         for (int iter = 0; iter < 8; ++iter) {
             ph = make_double2(std::cos(k * L), std::sin(k * L));
             k_lead_hk<<<dim3((n + 127) / 128, n), b128, 0, st>>>(n, ph, Ec, bz->H0.as<double2>(), bz->H1.as<double2>(),
@@ -304,8 +307,14 @@ int compute_lead_shared(const pwqt_ctx* bz, pwqt_ctx* c, const LeadWorker& wk, d
             PWQT_CUDA(c, cudaMemcpyAsync(hf, forms.p, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
             PWQT_CUDA(c, cudaStreamSynchronize(st));
             double w = hf[0], slope = hf[2];
-            if (std::fabs(w - Ec) < tol_E || slope == 0.0 || !std::isfinite(slope)) break;
+            if (std::fabs(w - Ec) < tol_E) { converged = true; break; }
+            if (slope == 0.0 || !std::isfinite(slope)) break;
             k -= (w - Ec) / slope;
+        }
+        if (!converged) {   // no traveling wave at this energy along this branch
+            trav[j] = 0;
+            status |= PWQT_ST_NEAR_UNIT;
+            continue;
         }
         hlam[j] = ph;
         dEdk[j] = hf[2];
@@ -315,20 +324,41 @@ int compute_lead_shared(const pwqt_ctx* bz, pwqt_ctx* c, const LeadWorker& wk, d
         k_scale_col<<<(n + 127) / 128, b128, 0, st>>>(Cm.as<double2>(), n, j, scale);
         launches++;
     }
-    // degenerate traveling modes (same lambda) are not flux-orthogonalised here: flag them
+    // two candidates refined onto the same mode: keep the first, reclassify the other by
+    // its raw |lambda|.  Distinct modes at the same lambda (a true degeneracy) are not
+    // flux-orthogonalised here: flag them.
     for (int a = 0; a < n2; ++a)
         for (int b = a + 1; b < n2; ++b)
-            if (trav[a] && trav[b] && std::hypot(hlam[a].x - hlam[b].x, hlam[a].y - hlam[b].y) < 1e-8) status |= PWQT_ST_DEGENERATE;
+            if (trav[a] && trav[b] && std::hypot(hlam[a].x - hlam[b].x, hlam[a].y - hlam[b].y) < 1e-8) {
+                if (std::fabs(dEdk[a] - dEdk[b]) < 1e-8 * std::max(1.0, std::fabs(dEdk[a]))) {
+                    trav[b] = 0;
+                    hlam[b] = raw_lam[b];
+                    status |= PWQT_ST_NEAR_UNIT;
+                } else {
+                    status |= PWQT_ST_DEGENERATE;
+                }
+            }
 
-    // ---- classification (drain convention lambda = c_{i+1}/c_i)
+    // ---- classification (drain convention lambda = c_{i+1}/c_i): sort the 2n modes into
+    // two sets of n by an out-flow score, log|lambda| for evanescent modes and -/+1e-5 for
+    // traveling modes with dE/dk >/< 0; the n lowest are the drain's out-flow modes, the
+    // n highest the source's (a nearly redundant basis makes the pencil close to singular,
+    // so spurious eigenvalues need not pair lambda <-> 1/lambda^*).
+    std::vector<double> score(n2);
+    for (int j = 0; j < n2; ++j)
+        score[j] = trav[j] ? (dEdk[j] > 0 ? -1e-5 : 1e-5) : std::log(std::max(std::hypot(hlam[j].x, hlam[j].y), 1e-300));
+    std::vector<int> order(n2);
+    for (int j = 0; j < n2; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return score[a] < score[b]; });
+    std::vector<char> is_out_d(n2, 0), is_out_s(n2, 0);
+    for (int q = 0; q < n; ++q) is_out_d[order[q]] = 1;
+    for (int q = n; q < n2; ++q) is_out_s[order[q]] = 1;
     std::vector<int> out_d, in_d, out_s, in_s;
     for (int j = 0; j < n2; ++j) {
-        double al = std::hypot(hlam[j].x, hlam[j].y);
-        if (trav[j]) {
-            if (dEdk[j] > 0) { out_d.push_back(j); in_s.push_back(j); }
-            else { out_s.push_back(j); in_d.push_back(j); }
-        } else if (al < 1.0) out_d.push_back(j);
-        else out_s.push_back(j);
+        if (is_out_d[j]) out_d.push_back(j);
+        else if (trav[j] && dEdk[j] < 0) in_d.push_back(j);
+        if (is_out_s[j]) out_s.push_back(j);
+        else if (trav[j] && dEdk[j] > 0) in_s.push_back(j);
     }
     auto E = std::make_unique<LeadEntry>();
     E->Ec = Ec;

@@ -1,13 +1,540 @@
-// Mixed-precision block sweep (placeholder until the tensor-core path lands).
+// Mixed-precision block sweep of [E M - H - Sigma] c = B (Eq. qtbm_system): complex64
+// factorisation with the products on the tensor cores (3xTF32 tcgen05 GEMM, FP32
+// accumulation), refined to FP64 residuals (Sec. 3.2 system, north of the
+// paper's own direct FP64 solve).
+//
+// Per node i, for every energy of the batch at once:
+//   form     F_i = E M0 - HV0_i (- Sigma at the ends),  XY_i = [U_i | b_i],  Lb = L_i
+//   Schur    [F_i | y-part of XY_i] -= L_i [X_{i-1} | y_{i-1}]               (tensor cores)
+//   LU       right-looking, 32-column panels with partial pivoting (FP32, one CTA
+//            per energy: pivot search, row swaps over F_i and XY_i, L-solve of the
+//            32-row strip), trailing update on the tensor cores
+//   U-solve  32-row blocks from the bottom: diagonal block (FP32) + update above
+//            (tensor cores)  ->  XY_i = [X_i | y_i]
+// then c_i = y_i - X_i c_{i+1} (tensor cores), FP64 copy, and refinement:
+//   r = B - A c (FP64), A d = r with the stored complex64 factors, c += d.
+#include <algorithm>
+#include <cmath>
+
+#include "cgemm_tc.cuh"
 #include "sweep_mixed.cuh"
 
 namespace pwqt {
 
-size_t mixed_bytes_per_energy(int, int, int) { return 0; }
+namespace {
 
-int solve_mixed(pwqt_ctx* c, System&, const SweepSys&, std::vector<SweepJob>&, SweepJob*, std::vector<ResJob>&, ResJob*, int,
-                int*, cudaStream_t) {
-    return fail(c, PWQT_ERR_INVALID_ARG, "mixed precision path not available in this build");
+constexpr int PW = 32;      // panel width
+constexpr int NT = 256;
+
+struct MixSys {
+    int n, N, m, w;                       // w = n + m (uniform m over the batch)
+    const double2* M0; const double2* M1; const double2* HV0; const double2* HV1;   // FP64 blocks
+    const float2* M1f; const float2* HV1f;                                         // complex64 copies
+    float2* F; long long sF;              // per energy N x n x n factors
+    int* piv; long long sP;               // per energy N x n pivot rows
+    float2* XY; long long sXY;            // per energy N x n x w
+    float2* Lb; long long sL;             // per energy n x n
+    double2* C64; double2* R64; long long sC;   // per energy N x n x m (FP64 solution, residual)
+    const SweepJob* jobs;
+};
+
+__device__ __forceinline__ float2 fmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ void ffma(float2& a, float2 b, float2 c) {
+    a.x = fmaf(b.x, c.x, fmaf(-b.y, c.y, a.x));
+    a.y = fmaf(b.x, c.y, fmaf(b.y, c.x, a.y));
+}
+__device__ __forceinline__ float2 fdiv(float2 a, float2 b) {
+    if (fabsf(b.x) >= fabsf(b.y)) {
+        float r = b.y / b.x, d = b.x + b.y * r;
+        return make_float2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+    }
+    float r = b.x / b.y, d = b.x * r + b.y;
+    return make_float2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+}
+__device__ __forceinline__ float2 to32(double2 v) { return make_float2((float)v.x, (float)v.y); }
+
+// ---------------------------------------------------------------- form the node blocks
+__global__ void k_mx_form(MixSys S, int i) {
+    const int e = blockIdx.y;
+    const SweepJob& J = S.jobs[e];
+    const int n = S.n, N = S.N, w = S.w, ms = J.ms, md = J.md;
+    const double E = J.E;
+    float2* F = S.F + e * S.sF + (size_t)i * n * n;
+    float2* XY = S.XY + e * S.sXY + (size_t)i * n * w;
+    float2* Lb = S.Lb + e * S.sL;
+    const double2* HV0 = S.HV0 + (size_t)i * n * n;
+    const double2* HV1 = S.HV1 + (size_t)i * n * n;
+    const double2* HVm = S.HV1 + (size_t)(i > 0 ? i - 1 : 0) * n * n;
+    const size_t nn = (size_t)n * n;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nn; t += (size_t)gridDim.x * blockDim.x) {
+        int r = (int)(t / n), c = (int)(t % n);
+        double2 d = csub(cscale(S.M0[t], E), HV0[t]);
+        if (i == 0 && J.sig_s) d = csub(d, J.sig_s[t]);
+        if (i == N - 1 && J.sig_d) d = csub(d, J.sig_d[t]);
+        F[t] = to32(d);
+        if (i > 0) {
+            size_t tt = (size_t)c * n + r;
+            Lb[t] = to32(cconj(csub(cscale(S.M1[tt], E), HVm[tt])));
+        }
+        XY[(size_t)r * w + c] = i < N - 1 ? to32(csub(cscale(S.M1[t], E), HV1[t])) : make_float2(0.f, 0.f);
+    }
+    const size_t nm = (size_t)n * S.m;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nm; t += (size_t)gridDim.x * blockDim.x) {
+        int r = (int)(t / S.m), g = (int)(t % S.m);
+        float2 v = make_float2(0.f, 0.f);
+        if (i == 0 && g < ms) v = to32(J.rhs_s[(size_t)r * ms + g]);
+        if (i == N - 1 && g >= ms && g < ms + md) v = to32(J.rhs_d[(size_t)r * md + (g - ms)]);
+        XY[(size_t)r * w + n + g] = v;
+    }
+}
+
+// ---------------------------------------------------------------- panel factorisation
+// Factor F_i[k0:n, k0:k0+wd] with partial pivoting (max |re|+|im|), apply the row
+// interchanges to the remaining columns of F_i and to XY_i, and solve the unit-lower
+// 32 x 32 block against the strip rows k0..k0+wd of [F_i right of the panel | XY_i].
+__global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd) {
+    extern __shared__ float2 P[];                     // (n - k0) x PW panel
+    __shared__ int prow[PW];
+    __shared__ float bv[NT / 32];
+    __shared__ int bi[NT / 32];
+    const int e = blockIdx.x;
+    const int n = S.n, w = S.w, rows = n - k0;
+    float2* F = S.F + e * S.sF + (size_t)i * n * n;
+    float2* XY = S.XY + e * S.sXY + (size_t)i * n * w;
+    int* piv = S.piv + e * S.sP + (size_t)i * n;
+    int st = 0;
+    for (int t = threadIdx.x; t < rows * PW; t += NT) {
+        int r = t / PW, c = t % PW;
+        P[t] = c < wd ? F[(size_t)(k0 + r) * n + k0 + c] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int j = 0; j < wd; ++j) {
+        float best = -1.f;
+        int idx = j;
+        for (int r = j + threadIdx.x; r < rows; r += NT) {
+            float2 v = P[r * PW + j];
+            float a = fabsf(v.x) + fabsf(v.y);
+            if (a > best) { best = a; idx = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            float ov = __shfl_down_sync(0xffffffff, best, o);
+            int oi = __shfl_down_sync(0xffffffff, idx, o);
+            if (ov > best || (ov == best && oi < idx)) { best = ov; idx = oi; }
+        }
+        if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = idx; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int q = 1; q < NT / 32; ++q)
+                if (bv[q] > bv[0] || (bv[q] == bv[0] && bi[q] < bi[0])) { bv[0] = bv[q]; bi[0] = bi[q]; }
+            prow[j] = bi[0];
+            piv[k0 + j] = k0 + bi[0];
+        }
+        __syncthreads();
+        const int p = prow[j];
+        if (p != j && threadIdx.x < PW) {
+            float2 a = P[j * PW + threadIdx.x];
+            P[j * PW + threadIdx.x] = P[p * PW + threadIdx.x];
+            P[p * PW + threadIdx.x] = a;
+        }
+        __syncthreads();
+        float2 pv = P[j * PW + j];
+        if (pv.x == 0.f && pv.y == 0.f) { st |= PWQT_ST_SINGULAR_PIVOT; pv = make_float2(1.f, 0.f); }
+        for (int r = j + 1 + threadIdx.x; r < rows; r += NT) P[r * PW + j] = fdiv(P[r * PW + j], pv);
+        __syncthreads();
+        const int cols = wd - j - 1;
+        for (int t = threadIdx.x; t < (rows - j - 1) * cols; t += NT) {
+            int r = j + 1 + t / cols, c = j + 1 + t % cols;
+            float2 l = P[r * PW + j];
+            ffma(P[r * PW + c], make_float2(-l.x, -l.y), P[j * PW + c]);
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < rows * wd; t += NT) {
+        int r = t / wd, c = t % wd;
+        F[(size_t)(k0 + r) * n + k0 + c] = P[r * PW + c];
+    }
+    // row interchanges on the other columns of F_i and on XY_i, in order
+    const int ncolF = n - wd;
+    for (int j = 0; j < wd; ++j) {
+        const int p = prow[j];
+        if (p == j) continue;
+        const int ra = k0 + j, rb = k0 + p;
+        for (int c = threadIdx.x; c < ncolF + w; c += NT) {
+            if (c < ncolF) {
+                int col = c < k0 ? c : c + wd;
+                float2 a = F[(size_t)ra * n + col]; F[(size_t)ra * n + col] = F[(size_t)rb * n + col]; F[(size_t)rb * n + col] = a;
+            } else {
+                int col = c - ncolF;
+                float2 a = XY[(size_t)ra * w + col]; XY[(size_t)ra * w + col] = XY[(size_t)rb * w + col]; XY[(size_t)rb * w + col] = a;
+            }
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    // strip: rows k0..k0+wd of [F cols k0+wd..n | XY] <- L11^{-1} strip (unit lower)
+    const int right = n - k0 - wd;
+    for (int c = threadIdx.x; c < right + w; c += NT) {
+        float2 x[PW];
+        float2* base;
+        size_t ld;
+        if (c < right) { base = F + (size_t)k0 * n + k0 + wd + c; ld = n; }
+        else { base = XY + (size_t)k0 * w + (c - right); ld = w; }
+#pragma unroll
+        for (int j = 0; j < PW; ++j) x[j] = j < wd ? base[(size_t)j * ld] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 1; j < PW; ++j) {
+            if (j < wd) {
+                float2 s = x[j];
+#pragma unroll
+                for (int l = 0; l < PW; ++l)
+                    if (l < j) {
+                        float2 L = P[j * PW + l];
+                        ffma(s, make_float2(-L.x, -L.y), x[l]);
+                    }
+                x[j] = s;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < PW; ++j)
+            if (j < wd) base[(size_t)j * ld] = x[j];
+    }
+    if (threadIdx.x == 0 && st) atomicOr(S.jobs[e].status, st);
+}
+
+// XY_i[k0:k0+wd, :] <- U11^{-1} XY_i[k0:k0+wd, :]
+__global__ void __launch_bounds__(NT) k_mx_trsm_up(MixSys S, int i, int k0, int wd) {
+    __shared__ float2 U[PW][PW + 1];
+    const int e = blockIdx.x;
+    const int n = S.n, w = S.w;
+    const float2* F = S.F + e * S.sF + (size_t)i * n * n;
+    float2* XY = S.XY + e * S.sXY + (size_t)i * n * w;
+    for (int t = threadIdx.x; t < PW * PW; t += NT) {
+        int r = t / PW, c = t % PW;
+        U[r][c] = (r < wd && c < wd) ? F[(size_t)(k0 + r) * n + k0 + c] : make_float2(r == c ? 1.f : 0.f, 0.f);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < w; c += NT) {
+        float2 x[PW];
+        float2* base = XY + (size_t)k0 * w + c;
+#pragma unroll
+        for (int j = 0; j < PW; ++j) x[j] = j < wd ? base[(size_t)j * w] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = PW - 1; j >= 0; --j) {
+            float2 s = x[j];
+#pragma unroll
+            for (int l = 0; l < PW; ++l)
+                if (l > j) ffma(s, make_float2(-U[j][l].x, -U[j][l].y), x[l]);
+            float2 d = U[j][j];
+            if (d.x == 0.f && d.y == 0.f) d = make_float2(1.f, 0.f);
+            x[j] = fdiv(s, d);
+        }
+#pragma unroll
+        for (int j = 0; j < PW; ++j)
+            if (j < wd) base[(size_t)j * w] = x[j];
+    }
+}
+
+// C64 = (double) c (the y columns of XY after the node back substitution)
+__global__ void k_mx_to64(MixSys S) {
+    const int e = blockIdx.y;
+    const int n = S.n, N = S.N, m = S.m, w = S.w;
+    const size_t tot = (size_t)N * n * m;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
+        size_t i = t / ((size_t)n * m), rem = t % ((size_t)n * m);
+        int r = (int)(rem / m), g = (int)(rem % m);
+        float2 v = S.XY[e * S.sXY + i * n * w + (size_t)r * w + n + g];
+        S.C64[e * S.sC + t] = make_double2(v.x, v.y);
+    }
+}
+
+// ---------------------------------------------------------------- correction solve
+// One CTA per energy: d = A^{-1} r with the stored factors (complex64), then c += d (FP64).
+// forward over nodes:  t_i = r_i - L_i w_{i-1};  w_i = U_i^{-1} L_i^{-1} P_i t_i
+// backward:            d_i = w_i - X_i d_{i+1}
+// w_i and d_i live in the y columns of XY_i.
+__global__ void __launch_bounds__(NT) k_mx_correct(MixSys S, const int* __restrict__ active) {
+    const int e = blockIdx.x;
+    if (!active[e]) return;
+    const SweepJob& J = S.jobs[e];
+    const int n = S.n, N = S.N, w = S.w, m = J.ms + J.md;
+    if (m == 0) return;
+    const float E = (float)J.E;
+    __shared__ float2 Ls[PW][PW + 1];
+    for (int i = 0; i < N; ++i) {
+        float2* XY = S.XY + e * S.sXY + (size_t)i * n * w;
+        const float2* XYp = S.XY + e * S.sXY + (size_t)(i > 0 ? i - 1 : 0) * n * w;
+        const float2* F = S.F + e * S.sF + (size_t)i * n * n;
+        const int* piv = S.piv + e * S.sP + (size_t)i * n;
+        const double2* R = S.R64 + e * S.sC + (size_t)i * n * S.m;
+        const float2* HVm = S.HV1f + (size_t)(i > 0 ? i - 1 : 0) * n * n;
+        // t = r - L_i w_{i-1},  L_i[r][k] = conj(E M1[k][r] - HV1_{i-1}[k][r])
+        for (int t = threadIdx.x; t < n * m; t += NT) {
+            int r = t / m, g = t % m;
+            float2 s = to32(R[(size_t)r * S.m + g]);
+            if (i > 0) {
+                for (int k = 0; k < n; ++k) {
+                    size_t kr = (size_t)k * n + r;
+                    float2 u = make_float2(E * S.M1f[kr].x - HVm[kr].x, E * S.M1f[kr].y - HVm[kr].y);
+                    ffma(s, make_float2(-u.x, u.y), XYp[(size_t)k * w + n + g]);   // -conj(u) * w
+                }
+            }
+            XY[(size_t)r * w + n + g] = s;
+        }
+        __syncthreads();
+        // row interchanges (each thread owns whole columns)
+        for (int g = threadIdx.x; g < m; g += NT)
+            for (int j = 0; j < n; ++j) {
+                int p = piv[j];
+                if (p != j) {
+                    float2 a = XY[(size_t)j * w + n + g];
+                    XY[(size_t)j * w + n + g] = XY[(size_t)p * w + n + g];
+                    XY[(size_t)p * w + n + g] = a;
+                }
+            }
+        __syncthreads();
+        // unit-lower forward solve, 32-row blocks
+        for (int kb = 0; kb < n; kb += PW) {
+            const int wd = min(PW, n - kb);
+            for (int t = threadIdx.x; t < PW * PW; t += NT) {
+                int r = t / PW, c = t % PW;
+                Ls[r][c] = (r < wd && c < wd) ? F[(size_t)(kb + r) * n + kb + c] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            for (int g = threadIdx.x; g < m; g += NT) {
+                for (int j = 1; j < wd; ++j) {
+                    float2 s = XY[(size_t)(kb + j) * w + n + g];
+                    for (int l = 0; l < j; ++l) ffma(s, make_float2(-Ls[j][l].x, -Ls[j][l].y), XY[(size_t)(kb + l) * w + n + g]);
+                    XY[(size_t)(kb + j) * w + n + g] = s;
+                }
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < (n - kb - wd) * m; t += NT) {
+                int r = kb + wd + t / m, g = t % m;
+                float2 s = XY[(size_t)r * w + n + g];
+                for (int l = 0; l < wd; ++l) {
+                    float2 L = F[(size_t)r * n + kb + l];
+                    ffma(s, make_float2(-L.x, -L.y), XY[(size_t)(kb + l) * w + n + g]);
+                }
+                XY[(size_t)r * w + n + g] = s;
+            }
+            __syncthreads();
+        }
+        // upper backward solve, 32-row blocks from the bottom
+        const int last = ((n - 1) / PW) * PW;
+        for (int kb = last; kb >= 0; kb -= PW) {
+            const int wd = min(PW, n - kb);
+            for (int t = threadIdx.x; t < PW * PW; t += NT) {
+                int r = t / PW, c = t % PW;
+                Ls[r][c] = (r < wd && c < wd) ? F[(size_t)(kb + r) * n + kb + c] : make_float2(r == c ? 1.f : 0.f, 0.f);
+            }
+            __syncthreads();
+            for (int g = threadIdx.x; g < m; g += NT) {
+                for (int j = wd - 1; j >= 0; --j) {
+                    float2 s = XY[(size_t)(kb + j) * w + n + g];
+                    for (int l = j + 1; l < wd; ++l) ffma(s, make_float2(-Ls[j][l].x, -Ls[j][l].y), XY[(size_t)(kb + l) * w + n + g]);
+                    float2 d = Ls[j][j];
+                    if (d.x == 0.f && d.y == 0.f) d = make_float2(1.f, 0.f);
+                    XY[(size_t)(kb + j) * w + n + g] = fdiv(s, d);
+                }
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < kb * m; t += NT) {
+                int r = t / m, g = t % m;
+                float2 s = XY[(size_t)r * w + n + g];
+                for (int l = 0; l < wd; ++l) {
+                    float2 U = F[(size_t)r * n + kb + l];
+                    ffma(s, make_float2(-U.x, -U.y), XY[(size_t)(kb + l) * w + n + g]);
+                }
+                XY[(size_t)r * w + n + g] = s;
+            }
+            __syncthreads();
+        }
+    }
+    // backward over nodes: d_i = w_i - X_i d_{i+1}
+    for (int i = N - 2; i >= 0; --i) {
+        float2* XY = S.XY + e * S.sXY + (size_t)i * n * w;
+        const float2* XYn = S.XY + e * S.sXY + (size_t)(i + 1) * n * w;
+        for (int t = threadIdx.x; t < n * m; t += NT) {
+            int r = t / m, g = t % m;
+            float2 s = XY[(size_t)r * w + n + g];
+            for (int k = 0; k < n; ++k) {
+                float2 X = XY[(size_t)r * w + k];
+                ffma(s, make_float2(-X.x, -X.y), XYn[(size_t)k * w + n + g]);
+            }
+            XY[(size_t)r * w + n + g] = s;
+        }
+        __syncthreads();
+    }
+    // c += d
+    for (size_t t = threadIdx.x; t < (size_t)N * n * m; t += NT) {
+        size_t i = t / ((size_t)n * m), rem = t % ((size_t)n * m);
+        int r = (int)(rem / m), g = (int)(rem % m);
+        float2 d = S.XY[e * S.sXY + i * n * w + (size_t)r * w + n + g];
+        double2& c = S.C64[e * S.sC + i * n * S.m + (size_t)r * S.m + g];
+        c.x += d.x;
+        c.y += d.y;
+    }
+}
+
+__global__ void k_or_status(const SweepJob* __restrict__ jobs, const int* __restrict__ bits, int nb) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb && bits[b]) atomicOr(jobs[b].status, bits[b]);
+}
+
+}  // namespace
+
+size_t mixed_bytes_per_energy(int n, int N, int m) {
+    // F + XY (complex64) + pivots + L scratch + FP64 solution and residual
+    return sizeof(float2) * ((size_t)N * n * n + (size_t)N * n * (n + m) + (size_t)n * n) + sizeof(int) * (size_t)N * n +
+           2 * sizeof(double2) * (size_t)N * n * m;
+}
+
+int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJob>& jobs, SweepJob* jobs_d, std::vector<ResJob>& res,
+                ResJob* res_d, std::vector<ObsJob>& obs, ObsJob* obs_d, int nb, int* iters_dev, cudaStream_t st) {
+    static bool inited = false;
+    if (!inited) {
+        if (cgemm_tc_init() != 0) return fail(c, PWQT_ERR_CUDA, "tensor-core GEMM set-up failed");
+        inited = true;
+    }
+    const int n = sys.n, N = sys.N;
+    int m = 0;
+    for (int b = 0; b < nb; ++b) m = std::max(m, jobs[b].ms + jobs[b].md);
+    m = std::max(m, 1);
+    const int w = n + m;
+    MixSys S;
+    S.n = n; S.N = N; S.m = m; S.w = w;
+    S.M0 = sys.M0; S.M1 = sys.M1; S.HV0 = sys.HV0; S.HV1 = sys.HV1;
+    S.M1f = c->M1f.as<float2>(); S.HV1f = s.HV1f.as<float2>();
+    S.sF = (long long)N * n * n;
+    S.sP = (long long)N * n;
+    S.sXY = (long long)N * n * w;
+    S.sL = (long long)n * n;
+    S.sC = (long long)N * n * m;
+    const size_t bytes = mixed_bytes_per_energy(n, N, m) * nb + 1024 * 4;
+    PWQT_TRY(ensure(c, c->ws_mixed, bytes));
+    char* base = c->ws_mixed.as<char>();
+    auto take = [&](size_t b) { char* p = base; base += (b + 255) / 256 * 256; return p; };
+    S.F = (float2*)take(sizeof(float2) * S.sF * nb);
+    S.XY = (float2*)take(sizeof(float2) * S.sXY * nb);
+    S.Lb = (float2*)take(sizeof(float2) * S.sL * nb);
+    S.piv = (int*)take(sizeof(int) * S.sP * nb);
+    S.C64 = (double2*)take(sizeof(double2) * S.sC * nb);
+    S.R64 = (double2*)take(sizeof(double2) * S.sC * nb);
+    S.jobs = jobs_d;
+    int* active_d = (int*)take(sizeof(int) * nb);
+    int* bits_d = (int*)take(sizeof(int) * nb);
+
+    // ---------------- forward sweep over the nodes
+    const int fblocks = (int)std::min<size_t>(((size_t)n * n + NT - 1) / NT, 512);
+    const size_t panel_smem = sizeof(float2) * (size_t)n * PW;
+    if (panel_smem > 48 * 1024)
+        PWQT_CUDA(c, cudaFuncSetAttribute(k_mx_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem));
+    auto gemm = [&](const float2* A, long long sA, int lda, const float2* B1, long long sB1, int ldb1, const float2* B2, long long sB2,
+                    int ldb2, float2* C1, long long sC1, int ldc1, float2* C2, long long sC2, int ldc2, int split, int M, int Nc, int K) {
+        CGemmArgs g{A, sA, lda, B1, sB1, ldb1, B2, sB2, ldb2, C1, sC1, ldc1, C2, sC2, ldc2, split};
+        launch_cgemm_tc(g, nb, M, Nc, K, st);
+        c->launches++;
+    };
+    if (c->profile) PWQT_CUDA(c, cudaEventRecord(c->ev0, st));
+    for (int i = 0; i < N; ++i) {
+        float2* Fi = S.F + (size_t)i * n * n;
+        float2* XYi = S.XY + (size_t)i * n * w;
+        k_mx_form<<<dim3(fblocks, nb), NT, 0, st>>>(S, i);
+        c->launches++;
+        if (i > 0) {
+            const float2* XYp = S.XY + (size_t)(i - 1) * n * w;
+            gemm(S.Lb, S.sL, n, XYp, S.sXY, w, XYp + n, S.sXY, w, Fi, S.sF, n, XYi + n, S.sXY, w, n, n, w, n);
+        }
+        for (int k0 = 0; k0 < n; k0 += PW) {
+            const int wd = std::min(PW, n - k0);
+            k_mx_panel<<<nb, NT, sizeof(float2) * (size_t)(n - k0) * PW, st>>>(S, i, k0, wd);
+            c->launches++;
+            const int rest = n - k0 - wd;
+            if (rest > 0)
+                gemm(Fi + (size_t)(k0 + wd) * n + k0, S.sF, n, Fi + (size_t)k0 * n + k0 + wd, S.sF, n, XYi + (size_t)k0 * w, S.sXY, w,
+                     Fi + (size_t)(k0 + wd) * n + k0 + wd, S.sF, n, XYi + (size_t)(k0 + wd) * w, S.sXY, w, rest, rest, rest + w, wd);
+        }
+        for (int k0 = ((n - 1) / PW) * PW; k0 >= 0; k0 -= PW) {
+            const int wd = std::min(PW, n - k0);
+            k_mx_trsm_up<<<nb, NT, 0, st>>>(S, i, k0, wd);
+            c->launches++;
+            if (k0 > 0) gemm(Fi + k0, S.sF, n, XYi + (size_t)k0 * w, S.sXY, w, XYi + (size_t)k0 * w, S.sXY, w, XYi, S.sXY, w, XYi, S.sXY,
+                             w, w, k0, w, wd);
+        }
+    }
+    // node back substitution c_i = y_i - X_i c_{i+1}
+    for (int i = N - 2; i >= 0; --i) {
+        float2* XYi = S.XY + (size_t)i * n * w;
+        const float2* XYn = S.XY + (size_t)(i + 1) * n * w;
+        gemm(XYi, S.sXY, w, XYn + n, S.sXY, w, XYn + n, S.sXY, w, XYi + n, S.sXY, w, XYi + n, S.sXY, w, m, n, m, n);
+    }
+    if (c->profile) {
+        PWQT_CUDA(c, cudaEventRecord(c->ev1, st));
+        PWQT_CUDA(c, cudaEventSynchronize(c->ev1));
+        float ms = 0;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        c->prof_ms += ms;
+        c->prof_launches += 1;
+        c->prof_flops += (56.0 / 3.0) * (double)N * n * n * (double)n * nb;
+    }
+    PWQT_CUDA(c, cudaGetLastError());
+    if (cgemm_tc_error(true)) return fail(c, PWQT_ERR_CUDA, "tensor-core GEMM wait timed out");
+    k_mx_to64<<<dim3(256, nb), NT, 0, st>>>(S);
+    c->launches++;
+
+    // ---------------- refinement with FP64 residuals
+    for (int b = 0; b < nb; ++b) {
+        res[b].C = S.C64 + S.sC * b;
+        res[b].node_stride = (size_t)n * m;
+        res[b].row_stride = m;
+        res[b].Rout = S.R64 + S.sC * b;
+        res[b].r_node_stride = (size_t)n * m;
+        res[b].r_row_stride = m;
+    }
+    PWQT_CUDA(c, cudaMemcpyAsync(res_d, res.data(), sizeof(ResJob) * nb, cudaMemcpyHostToDevice, st));
+    std::vector<double> resid(nb, 1.0), prev(nb, 1e300);
+    std::vector<int> iters(nb, 0), active(nb, 1), stall(nb, 0), bits(nb, 0);
+    const double tol = c->opts.ir_tol;
+    for (int it = 0;; ++it) {
+        PWQT_CUDA(c, cudaMemsetAsync(res[0].rn2, 0, sizeof(double) * 2 * (size_t)nb * m, st));
+        launch_residual_fp64(sys, res_d, nb, st);
+        c->launches += 2;
+        PWQT_CUDA(c, cudaMemcpyAsync(resid.data(), res[0].resid, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+        PWQT_CUDA(c, cudaStreamSynchronize(st));
+        int any = 0;
+        for (int b = 0; b < nb; ++b) {
+            if (!active[b]) continue;
+            if (resid[b] <= tol) { active[b] = 0; continue; }
+            if (resid[b] > 0.5 * prev[b]) stall[b]++;
+            else stall[b] = 0;
+            if (stall[b] >= 3 || iters[b] >= c->opts.ir_max_iters) {
+                active[b] = 0;
+                bits[b] |= PWQT_ST_IR_NO_CONVERGE;
+                continue;
+            }
+            prev[b] = std::min(prev[b], resid[b]);
+            iters[b]++;
+            any = 1;
+        }
+        if (!any) break;
+        PWQT_CUDA(c, cudaMemcpyAsync(active_d, active.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+        k_mx_correct<<<nb, NT, 0, st>>>(S, active_d);
+        c->launches++;
+        PWQT_CUDA(c, cudaGetLastError());
+    }
+    PWQT_CUDA(c, cudaMemcpyAsync(iters_dev, iters.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+    PWQT_CUDA(c, cudaMemcpyAsync(bits_d, bits.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+    k_or_status<<<(nb + 127) / 128, 128, 0, st>>>(jobs_d, bits_d, nb);
+    c->launches++;
+    // observables read c from the FP64 solution
+    for (int b = 0; b < nb; ++b) {
+        obs[b].C = S.C64 + S.sC * b;
+        obs[b].node_stride = (size_t)n * m;
+        obs[b].row_stride = m;
+    }
+    PWQT_CUDA(c, cudaMemcpyAsync(obs_d, obs.data(), sizeof(ObsJob) * nb, cudaMemcpyHostToDevice, st));
+    PWQT_CUDA(c, cudaStreamSynchronize(st));
+    return PWQT_OK;
 }
 
 }  // namespace pwqt

@@ -30,6 +30,7 @@ void launch_residual_fp64(const SweepSys& sys, const ResJob* jobs, int nb, cudaS
 
 size_t mixed_bytes_per_energy(int n, int N, int m);
 int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJob>& jobs, SweepJob* jobs_d,
-                std::vector<ResJob>& res, ResJob* res_d, int nb, int* iters_dev, cudaStream_t st);
+                std::vector<ResJob>& res, ResJob* res_d, std::vector<ObsJob>& obs, ObsJob* obs_d, int nb, int* iters_dev,
+                cudaStream_t st);
 
 }  // namespace pwqt

@@ -22,7 +22,7 @@ ST_SINGULAR_PIVOT, ST_MODE_COUNT, ST_IR_NO_CONVERGE, ST_DEGENERATE, ST_NEAR_UNIT
 
 EXPORTS = ["pwqt_create", "pwqt_destroy", "pwqt_last_error", "pwqt_assemble_intrinsic", "pwqt_set_enhancement",
            "pwqt_get_blocks", "pwqt_set_extrinsic", "pwqt_solve", "pwqt_solve_dev", "pwqt_prepare_leads",
-           "pwqt_cache_info", "pwqt_bands", "pwqt_kernel_launches", "pwqt_profile", "pwqt_solve_noalloc"]
+           "pwqt_cache_info", "pwqt_bands", "pwqt_kernel_launches", "pwqt_profile", "pwqt_solve_noalloc", "pwqt_cgemm_c64"]
 
 
 class PwqtError(RuntimeError):
@@ -74,6 +74,8 @@ def load(path: str = LIB_PATH):
     lib.pwqt_kernel_launches.argtypes = [P, C.POINTER(C.c_longlong), I]
     lib.pwqt_profile.argtypes = [P, I, dp, C.POINTER(C.c_longlong), dp, I]
     lib.pwqt_solve_noalloc.argtypes = [P, I, I, dp, P, P, P, P, P, P]
+    fp = C.POINTER(C.c_float)
+    lib.pwqt_cgemm_c64.argtypes = [I, I, I, I, fp, I, fp, I, fp, I]
     for f in EXPORTS:
         if f != "pwqt_last_error":
             getattr(lib, f).restype = C.c_int
@@ -105,6 +107,22 @@ class SolveResult:
     resid: np.ndarray
     iters: np.ndarray
     status: np.ndarray
+
+
+def cgemm_c64(a, b, c):
+    """c -= a @ b on the tensor cores for batched complex64 arrays (batch, M, K), (batch, K, N),
+    (batch, M, N); returns the updated copy of c."""
+    lib = load()
+    a = np.ascontiguousarray(a, dtype=np.complex64)
+    b = np.ascontiguousarray(b, dtype=np.complex64)
+    out = np.array(c, dtype=np.complex64, order="C", copy=True)
+    nb, M, K = a.shape
+    N = b.shape[2]
+    fp = lambda x: x.ctypes.data_as(C.POINTER(C.c_float))
+    r = lib.pwqt_cgemm_c64(nb, M, N, K, fp(a), K, fp(b), N, fp(out), N)
+    if r != PWQT_OK:
+        raise PwqtError(r, "pwqt_cgemm_c64 failed")
+    return out
 
 
 class Context:

@@ -156,6 +156,9 @@ class Workload:
 # spin-degenerate bands).  Written by oracle/derive_workload_constants.py.
 RIBBON15_G45_ECB = 15.4042629215437
 RIBBON15_G60_ECB = 15.404261893989412
+# Bottom of band index 64 (minimum over Gamma and Z) of the 13 nm armchair ribbon at
+# G_cut = 30 nm^-1.  Written by oracle/derive_workload_constants.py.
+RIBBON13_G30_E64 = 3.204472869713024
 
 
 def chain8(n_nodes: int = 20, n_energies: int = 64) -> Workload:
@@ -183,8 +186,26 @@ def ribbon256(n_nodes: int = 200, n_energies: int = 1024) -> Workload:
 
 
 def ribbon512(n_nodes: int = 200, n_energies: int = 1024) -> Workload:
-    """Metric workload: same ribbon at G_cut = 60 nm^-1, block 512, 200 nodes, 1024 energies."""
-    return _ribbon("ribbon512", 60.0, 256, n_nodes, n_energies, RIBBON15_G60_ECB)
+    """Block-512 workload: 13 nm armchair ribbon (214 atoms per cell), 256 Bloch waves
+    at Gamma and at Z (G_cut = 30 nm^-1), 200 nodes, 1024 energies on
+    [E_64 - 0.1, E_64 + 1.0] eV (about 45 open channels per contact).
+
+    The PU basis of 256 bands per k-point on the 1.5 nm ribbon (26 atoms) is
+    numerically redundant (smallest/largest eigenvalue of M(k) ~ 4e-10, lead pencil
+    cond ~ 1e16); on this wider ribbon the same block size keeps ~1.2 bands per atom
+    (M(k) ratio ~ 2e-5, lead pencil cond ~ 4e6)."""
+    cell = armchair_ribbon_cell(ribbon_lines_for_width(13.0))
+    e0 = RIBBON13_G30_E64
+    return Workload("ribbon512", cell, FormFactor(), 30.0, 256, n_nodes,
+                    midpoint_grid(e0 - 0.1, e0 + 1.0, n_energies),
+                    random_smooth(n_nodes, 0.3, 20190301),
+                    notes="armchair ribbon 13 nm, block 512, random smooth U <= 0.3 eV")
+
+
+def ribbon512_narrow(n_nodes: int = 200, n_energies: int = 1024) -> Workload:
+    """The 1.5 nm ribbon at G_cut = 60 nm^-1 with 256 bands per k-point (block 512):
+    kept to document the numerically redundant basis (not a benchmark workload)."""
+    return _ribbon("ribbon512_narrow", 60.0, 256, n_nodes, n_energies, RIBBON15_G60_ECB)
 
 
 def small_ribbon(n_bands: int = 16, n_nodes: int = 8, n_energies: int = 8,

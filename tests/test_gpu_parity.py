@@ -209,3 +209,47 @@ def test_chain_parity_statistics(pw, chain):
     print(f"T parity: max |dT| = {d.max():.2e}, {100 * within:.0f}% of energies within 1e-9")
     assert within >= 0.75
     assert d.max() < 1e-7
+
+
+# ---------------------------------------------------------------- mixed precision
+# complex64 factorisation on the tensor cores (3xTF32) + refinement with FP64
+# residuals: T within 1e-8 of the oracle (or 4x the two sides' reciprocity defects)
+MIXED_TOL = 1e-8
+
+
+def test_mixed_chain_all_energies(pw, chain):
+    wl, s = chain
+    ctx = _ctx_with_basis(pw, s)
+    ctx.set_extrinsic(0, wl.U)
+    res = ctx.solve(0, wl.energies, pw.MIXED)
+    ref = _oracle_results(s, wl.energies)
+    _compare(res, ref, tol=MIXED_TOL)
+    open_e = res.n_open.sum(1) > 0
+    assert np.all(res.iters[open_e] >= 1)
+    assert np.max(res.resid) <= 1e-10
+    assert np.all(res.status == 0)
+
+
+def test_mixed_small_ribbon(pw):
+    from tests.oracle_fixtures import small_ribbon_system
+    s = small_ribbon_system()
+    ctx = _ctx_with_basis(pw, s)
+    ctx.set_extrinsic(0, s.U)
+    Es = np.array([0.25, 0.6, 1.1, 1.7, 2.3])
+    res = ctx.solve(0, Es, pw.MIXED)
+    _compare(res, _oracle_results(s, Es), tol=MIXED_TOL)
+    assert np.max(res.resid) <= 1e-10
+
+
+def test_mixed_matches_fp64_path_on_a_longer_ribbon(pw):
+    # several 32-column panels and a ragged last panel (n = 72), 24 nodes
+    from tests.oracle_fixtures import small_ribbon_system
+    s = small_ribbon_system(n_bands=36, n_nodes=24, gcut=30.0)
+    ctx = _ctx_with_basis(pw, s)
+    ctx.set_extrinsic(0, s.U)
+    Es = np.array([0.4, 1.3, 2.1])
+    r64 = ctx.solve(0, Es, pw.FP64)
+    rmx = ctx.solve(0, Es, pw.MIXED)
+    t = np.maximum(MIXED_TOL * np.maximum(1, r64.n_open[:, 0]), 4 * np.abs(r64.T - r64.T_ds))
+    assert np.all(np.abs(rmx.T - r64.T) <= t + 4 * np.abs(rmx.T - rmx.T_ds))
+    assert np.all(rmx.status & ~pw.ST_NEAR_UNIT == 0)

@@ -19,7 +19,10 @@ def _pins_hold(sys_):
     band reconstruction at Gamma and Z."""
     blk = sys_.blk
     for E in (0.3, 1.0):
-        r = O.solve_energy(blk, sys_.Vd, sys_.Vu, sys_.U, E)
+        try:
+            r = O.solve_energy(blk, sys_.Vd, sys_.Vu, sys_.U, E)
+        except RuntimeError:          # a broken contact (mode count) also fails the pins
+            return False
         if not (abs(r.T - 1.0) < 1e-8 and abs(r.R) < 1e-8):
             return False
     for gi, kp in ((0, 0.0), (1, math.pi / blk["L"])):
