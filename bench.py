@@ -1,10 +1,13 @@
 """Benchmark: energy-solves/s of the per-energy open-boundary solve at block size 512.
 
-Workload (default): the 1.5 nm armchair ribbon at G_cut = 60 nm^-1, block n = 512
-(256 Bloch waves at Gamma and at Z), N = 200 nodes, a seeded smooth potential
-<= 0.3 eV, and the 1024-point energy grid [E_cb - 0.1, E_cb + 1.0] eV; one step
-solves one batch of energies of that grid (contact self-energies resident in the
-cache, built before timing and reported separately as sigma_cold_s_per_energy).
+Workload (default, "ribbon512"): a 13 nm armchair ribbon (214 atoms per cell) with
+256 Bloch waves at Gamma and at Z (block n = 512, G_cut = 30 nm^-1), N = 200 nodes, a
+seeded smooth potential <= 0.3 eV and the 1024-point energy grid
+[E_64 - 0.1, E_64 + 1.0] eV (~45 open channels per contact); one step solves one
+batch of energies of that grid (contact self-energies resident in the cache, built
+before timing and reported separately as sigma_cold_s_per_energy).  Default path:
+complex64 block sweep on the tensor cores + refinement; --precision fp64 times the
+complex128 path.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                 [--precision mixed|fp64|auto] [--batch B]
@@ -212,7 +215,7 @@ def run_ours(args, world, rank, local):
     if prec_name == "auto":
         prec_name = "mixed"
     prec = pw.MIXED if prec_name == "mixed" else pw.FP64
-    batch = args.batch or (152 if prec == pw.FP64 else 304)
+    batch = args.batch or (152 if prec == pw.FP64 else 64)
     n_grid = len(wl.energies)
     idx = (np.arange(batch) * max(1, n_grid // batch) + rank * batch) % n_grid
     E = np.sort(wl.energies[idx])
@@ -312,7 +315,8 @@ def run_ours(args, world, rank, local):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == pw.FP64 else "c64/tf32+f64",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == pw.FP64 else "c64 (3xTF32 tensor cores) + float-float residual",
             "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "nodes": N, "energies_per_step": batch,
                        "energy_grid": n_grid, "precision": prec_name, "l2": "inputs larger than L2 "

@@ -14,6 +14,7 @@
 #include <numeric>
 
 #include "pwqt_internal.cuh"
+#include "sweep_mixed.cuh"
 
 namespace pwqt {
 
@@ -377,6 +378,11 @@ int assemble_from_basis(pwqt_ctx* c, const pwqt_cell* cell, int n_bands, const d
     c128_to_c64(c->H0.as<double2>(), c->H0f.as<float2>(), nn, c->stream);
     c128_to_c64(c->H1.as<double2>(), c->H1f.as<float2>(), nn, c->stream);
     c->launches += 4;
+    PWQT_TRY(alloc(c, c->M0ff, sizeof(float4) * nn));
+    PWQT_TRY(alloc(c, c->M1ff, sizeof(float4) * nn));
+    split_ff(c->M0.as<double2>(), c->M0ff.as<float4>(), nn, c->stream);
+    split_ff(c->M1.as<double2>(), c->M1ff.as<float4>(), nn, c->stream);
+    c->launches += 2;
     PWQT_CUDA(c, cudaStreamSynchronize(c->stream));
     c->n = n;
     c->n_bands = nb;
@@ -425,6 +431,11 @@ int build_system_blocks(pwqt_ctx* c, System& s) {
     PWQT_TRY(alloc(c, s.HV1f, sizeof(float2) * nn * std::max(N - 1, 1)));
     c128_to_c64(s.HV0.as<double2>(), s.HV0f.as<float2>(), nn * N, c->stream);
     c128_to_c64(s.HV1.as<double2>(), s.HV1f.as<float2>(), nn * (N - 1), c->stream);
+    c->launches += 2;
+    PWQT_TRY(alloc(c, s.HV0ff, sizeof(float4) * nn * N));
+    PWQT_TRY(alloc(c, s.HV1ff, sizeof(float4) * nn * std::max(N - 1, 1)));
+    split_ff(s.HV0.as<double2>(), s.HV0ff.as<float4>(), nn * N, c->stream);
+    split_ff(s.HV1.as<double2>(), s.HV1ff.as<float4>(), nn * (N - 1), c->stream);
     c->launches += 2;
     PWQT_CUDA(c, cudaStreamSynchronize(c->stream));
     return PWQT_OK;

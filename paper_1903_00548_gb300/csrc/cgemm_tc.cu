@@ -13,8 +13,11 @@
 // Tile: 128 rows x 128 complex columns (256 real accumulator columns = 256 TMEM
 // columns), K staged 32 complex (64 real) at a time in shared memory, operands
 // in the canonical K-major no-swizzle layout (8-row x 16-byte core matrices).
-// One thread issues the MMAs and commits them to an mbarrier; the four warps
-// read the accumulator back with tcgen05.ld and apply C -= acc.
+// One thread issues the MMAs and commits them to an mbarrier.  The tensor cores'
+// FP32 accumulation truncates, so each 32-complex K stage starts a fresh TMEM
+// accumulation and the eight warps add the stage result into FP32 registers
+// (round to nearest): truncation then accrues over one stage (24 MMAs), not all
+// of K.  Warps w and w + 4 read TMEM lanes 32 (w % 4).. and hold 128 columns each.
 #include <cstdint>
 
 #include "cgemm_tc.cuh"
@@ -28,7 +31,7 @@ constexpr int BNC = 128;           // complex columns per tile
 constexpr int BKC = 32;            // complex K per stage
 constexpr int BNR = 2 * BNC;       // 256 real accumulator columns
 constexpr int BKR = 2 * BKC;       // 64 real K per stage
-constexpr int THREADS = 128;
+constexpr int THREADS = 256;       // warps w and w+4 share TMEM lanes 32(w%4).. (column halves)
 constexpr uint32_t CORE_BYTES = 128;                 // 8 rows x 16 bytes
 constexpr uint32_t LBO = CORE_BYTES;                 // next 16-byte chunk along K
 constexpr uint32_t SBO = (BKR * 4 / 16) * CORE_BYTES;   // next 8-row group: 16 chunks x 128 B = 2048 B
@@ -90,6 +93,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
     return false;
 }
 
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
 __global__ void __launch_bounds__(THREADS, 1)
 k_cgemm_tc(const CGemmArgs G, int M, int N, int K) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -122,6 +137,10 @@ k_cgemm_tc(const CGemmArgs G, int M, int N, int K) {
     const uint32_t tmem = *tmem_slot;
     uint32_t phase = 0;
     bool ok = true;
+    const int colhalf = (warp >> 2) * 128;     // accumulator columns owned by this warp
+    float acc[128];
+#pragma unroll
+    for (int j = 0; j < 128; ++j) acc[j] = 0.f;
 
     const int nstages = (K + BKC - 1) / BKC;
     for (int s = 0; s < nstages && ok; ++s) {
@@ -158,7 +177,7 @@ k_cgemm_tc(const CGemmArgs G, int M, int N, int K) {
             const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
             for (int ks = 0; ks < BKR / 8; ++ks) {
                 const uint32_t koff = (uint32_t)ks * 2 * LBO;   // 8 real K = two 16-byte chunks
-                const uint32_t first = (s == 0 && ks == 0) ? 0u : 1u;
+                const uint32_t first = ks == 0 ? 0u : 1u;   // every stage restarts the accumulation
                 mma_tf32(tmem, make_desc(ah + koff), make_desc(bh + koff), first);
                 mma_tf32(tmem, make_desc(ah + koff), make_desc(bl + koff), 1u);
                 mma_tf32(tmem, make_desc(al + koff), make_desc(bh + koff), 1u);
@@ -168,38 +187,36 @@ k_cgemm_tc(const CGemmArgs G, int M, int N, int K) {
         // the next stage overwrites shared memory: wait until the MMAs have read it
         ok = mbar_wait(smem_u32(mbar), phase);
         phase ^= 1u;
+        if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+            for (int c = 0; c < 128; c += 32) {
+                uint32_t v[32];
+                const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(colhalf + c);
+                tmem_ld32(taddr, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[c + j] += __uint_as_float(v[j]);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+        }
         __syncthreads();
     }
     if (!ok) {
         if (tid == 0) atomicExch(&g_tc_error, 1);
         mbar_wait(smem_u32(mbar), phase ^ 1u);   // bounded second wait for the MMAs in flight
     } else {
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        // ---- epilogue: warp w owns TMEM lanes 32w..32w+31 = tile rows
-        const int r = row0 + warp * 32 + (tid & 31);
-        for (int c = 0; c < BNR; c += 32) {
-            uint32_t v[32];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-                  "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-                  "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
-            if (r < M) {
+        // ---- epilogue: C -= acc; this thread owns tile row (warp % 4) * 32 + lane, columns colhalf..+128
+        const int r = row0 + (warp & 3) * 32 + (tid & 31);
+        if (r < M) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    int cc = col0 + c / 2 + j;
-                    if (cc < N) {
-                        float2* p = cc < J.split ? J.C1 + (size_t)r * J.ldc1 + cc : J.C2 + (size_t)r * J.ldc2 + (cc - J.split);
-                        float2 o = *p;
-                        o.x -= __uint_as_float(v[2 * j]);
-                        o.y -= __uint_as_float(v[2 * j + 1]);
-                        *p = o;
-                    }
+            for (int j = 0; j < 64; ++j) {
+                const int cc = col0 + colhalf / 2 + j;
+                if (cc < N) {
+                    float2* p = cc < J.split ? J.C1 + (size_t)r * J.ldc1 + cc : J.C2 + (size_t)r * J.ldc2 + (cc - J.split);
+                    float2 o = *p;
+                    o.x -= acc[2 * j];
+                    o.y -= acc[2 * j + 1];
+                    *p = o;
                 }
             }
         }

@@ -95,6 +95,7 @@ struct System {
     std::vector<double> U;
     DBuf HV0, HV1;        // N and N-1 blocks: H_ii + V_ii, H_{i,i+1} + V_{i,i+1} (complex128)
     DBuf HV0f, HV1f;      // complex64 copies (mixed path)
+    DBuf HV0ff, HV1ff;    // float-float splits (refinement residual)
 };
 
 }  // namespace pwqt
@@ -115,6 +116,7 @@ struct pwqt_ctx {
     std::vector<double> eps;               // 2 n_bands
     pwqt::DBuf H0, H1, M0, M1, W;          // n x n row-major complex128; W: 6 blocks
     pwqt::DBuf M0f, M1f, H0f, H1f;         // complex64 copies
+    pwqt::DBuf M0ff, M1ff;                 // float-float splits
     std::map<int, pwqt::System> systems;
     std::map<double, std::unique_ptr<pwqt::LeadEntry>> cache;
     // scratch reused across calls

@@ -123,10 +123,14 @@ __global__ void k_residual_finish(const ResJob* __restrict__ jobs, int nb) {
     *J.resid = worst;
 }
 
+void launch_residual_finish(const ResJob* jobs, int nb, cudaStream_t st) {
+    k_residual_finish<<<(nb + 127) / 128, 128, 0, st>>>(jobs, nb);
+}
+
 void launch_residual_fp64(const SweepSys& sys, const ResJob* jobs, int nb, cudaStream_t st) {
     dim3 grid(sys.N, nb);
     k_residual_fp64<<<grid, 256, 0, st>>>(sys, jobs);
-    k_residual_finish<<<(nb + 127) / 128, 128, 0, st>>>(jobs, nb);
+    launch_residual_finish(jobs, nb, st);
 }
 
 __global__ void k_fill_int(int* p, int v, int cnt) {

@@ -54,7 +54,7 @@ __device__ __forceinline__ float2 fdiv(float2 a, float2 b) {
 __device__ __forceinline__ float2 to32(double2 v) { return make_float2((float)v.x, (float)v.y); }
 
 // ---------------------------------------------------------------- form the node blocks
-__global__ void k_mx_form(MixSys S, int i) {
+__global__ void k_mx_form(MixSys S, int i, int only_L) {
     const int e = blockIdx.y;
     const SweepJob& J = S.jobs[e];
     const int n = S.n, N = S.N, w = S.w, ms = J.ms, md = J.md;
@@ -66,6 +66,14 @@ __global__ void k_mx_form(MixSys S, int i) {
     const double2* HV1 = S.HV1 + (size_t)i * n * n;
     const double2* HVm = S.HV1 + (size_t)(i > 0 ? i - 1 : 0) * n * n;
     const size_t nn = (size_t)n * n;
+    if (only_L) {
+        for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nn; t += (size_t)gridDim.x * blockDim.x) {
+            int r = (int)(t / n), c = (int)(t % n);
+            size_t tt = (size_t)c * n + r;
+            Lb[t] = to32(cconj(csub(cscale(S.M1[tt], E), HVm[tt])));
+        }
+        return;
+    }
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nn; t += (size_t)gridDim.x * blockDim.x) {
         int r = (int)(t / n), c = (int)(t % n);
         double2 d = csub(cscale(S.M0[t], E), HV0[t]);
@@ -248,129 +256,134 @@ __global__ void k_mx_to64(MixSys S) {
 }
 
 // ---------------------------------------------------------------- correction solve
-// One CTA per energy: d = A^{-1} r with the stored factors (complex64), then c += d (FP64).
-// forward over nodes:  t_i = r_i - L_i w_{i-1};  w_i = U_i^{-1} L_i^{-1} P_i t_i
-// backward:            d_i = w_i - X_i d_{i+1}
-// w_i and d_i live in the y columns of XY_i.
-__global__ void __launch_bounds__(NT) k_mx_correct(MixSys S, const int* __restrict__ active) {
+// d = A^{-1} r with the stored complex64 factors; the y columns of XY_i hold the work
+// vectors.  Per node (all energies at once):  w_i = r_i - L_i w_{i-1}  (tensor cores),
+// w_i <- U_i^{-1} L_i^{-1} P_i w_i (k_mx_lusolve); then d_i = w_i - X_i d_{i+1}
+// (tensor cores) from the last node back, and c += d in FP64.
+
+// w_i = (complex64) r_i   (active energies)
+__global__ void k_mx_load_r(MixSys S, int i, const int* __restrict__ active) {
+    const int e = blockIdx.y;
+    if (!active[e]) return;
+    const int n = S.n, w = S.w, m = S.m;
+    float2* XY = S.XY + e * S.sXY + (size_t)i * n * w;
+    const double2* R = S.R64 + e * S.sC + (size_t)i * n * m;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)n * m; t += (size_t)gridDim.x * blockDim.x) {
+        int r = (int)(t / m), g = (int)(t % m);
+        XY[(size_t)r * w + n + g] = to32(R[t]);
+    }
+}
+
+// w <- U^{-1} L^{-1} P w for node i: one CTA per energy; pivots composed into a
+// permutation, 32-row diagonal blocks solved in shared memory, off-diagonal updates
+// in parallel over (row, column).
+__global__ void __launch_bounds__(NT) k_mx_lusolve(MixSys S, int i, const int* __restrict__ active) {
     const int e = blockIdx.x;
     if (!active[e]) return;
     const SweepJob& J = S.jobs[e];
-    const int n = S.n, N = S.N, w = S.w, m = J.ms + J.md;
+    const int n = S.n, w = S.w, m = J.ms + J.md;
     if (m == 0) return;
-    const float E = (float)J.E;
-    __shared__ float2 Ls[PW][PW + 1];
-    for (int i = 0; i < N; ++i) {
-        float2* XY = S.XY + e * S.sXY + (size_t)i * n * w;
-        const float2* XYp = S.XY + e * S.sXY + (size_t)(i > 0 ? i - 1 : 0) * n * w;
-        const float2* F = S.F + e * S.sF + (size_t)i * n * n;
-        const int* piv = S.piv + e * S.sP + (size_t)i * n;
-        const double2* R = S.R64 + e * S.sC + (size_t)i * n * S.m;
-        const float2* HVm = S.HV1f + (size_t)(i > 0 ? i - 1 : 0) * n * n;
-        // t = r - L_i w_{i-1},  L_i[r][k] = conj(E M1[k][r] - HV1_{i-1}[k][r])
-        for (int t = threadIdx.x; t < n * m; t += NT) {
-            int r = t / m, g = t % m;
-            float2 s = to32(R[(size_t)r * S.m + g]);
-            if (i > 0) {
-                for (int k = 0; k < n; ++k) {
-                    size_t kr = (size_t)k * n + r;
-                    float2 u = make_float2(E * S.M1f[kr].x - HVm[kr].x, E * S.M1f[kr].y - HVm[kr].y);
-                    ffma(s, make_float2(-u.x, u.y), XYp[(size_t)k * w + n + g]);   // -conj(u) * w
-                }
-            }
-            XY[(size_t)r * w + n + g] = s;
+    extern __shared__ unsigned char sm[];
+    int* perm = reinterpret_cast<int*>(sm);                                  // n
+    float2* Ld = reinterpret_cast<float2*>(sm + ((n * sizeof(int) + 15) / 16) * 16);   // PW x (PW+1)
+    float2* strip = Ld + PW * (PW + 1);                                       // PW x m
+    const float2* F = S.F + e * S.sF + (size_t)i * n * n;
+    const int* piv = S.piv + e * S.sP + (size_t)i * n;
+    float2* W = S.XY + e * S.sXY + (size_t)i * n * w + n;     // row stride w
+    float2* T = S.Lb + e * S.sL;                               // n x m scratch, row stride m
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < n; ++j) perm[j] = j;
+        for (int j = 0; j < n; ++j) {
+            int p = piv[j];
+            if (p != j) { int a = perm[j]; perm[j] = perm[p]; perm[p] = a; }
         }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n * m; t += NT) {
+        int r = t / m, g = t % m;
+        T[(size_t)r * m + g] = W[(size_t)perm[r] * w + g];
+    }
+    __syncthreads();
+    // forward, unit lower
+    for (int kb = 0; kb < n; kb += PW) {
+        const int wd = min(PW, n - kb);
+        for (int t = threadIdx.x; t < PW * PW; t += NT) {
+            int r = t / PW, c = t % PW;
+            Ld[r * (PW + 1) + c] = (r < wd && c < wd) ? F[(size_t)(kb + r) * n + kb + c] : make_float2(0.f, 0.f);
+        }
+        for (int t = threadIdx.x; t < wd * m; t += NT) strip[t] = T[(size_t)(kb + t / m) * m + t % m];
         __syncthreads();
-        // row interchanges (each thread owns whole columns)
         for (int g = threadIdx.x; g < m; g += NT)
-            for (int j = 0; j < n; ++j) {
-                int p = piv[j];
-                if (p != j) {
-                    float2 a = XY[(size_t)j * w + n + g];
-                    XY[(size_t)j * w + n + g] = XY[(size_t)p * w + n + g];
-                    XY[(size_t)p * w + n + g] = a;
+            for (int j = 1; j < wd; ++j) {
+                float2 a = strip[j * m + g];
+                for (int l = 0; l < j; ++l) {
+                    float2 L = Ld[j * (PW + 1) + l];
+                    ffma(a, make_float2(-L.x, -L.y), strip[l * m + g]);
                 }
+                strip[j * m + g] = a;
             }
         __syncthreads();
-        // unit-lower forward solve, 32-row blocks
-        for (int kb = 0; kb < n; kb += PW) {
-            const int wd = min(PW, n - kb);
-            for (int t = threadIdx.x; t < PW * PW; t += NT) {
-                int r = t / PW, c = t % PW;
-                Ls[r][c] = (r < wd && c < wd) ? F[(size_t)(kb + r) * n + kb + c] : make_float2(0.f, 0.f);
+        for (int t = threadIdx.x; t < wd * m; t += NT) T[(size_t)(kb + t / m) * m + t % m] = strip[t];
+        for (int t = threadIdx.x; t < (n - kb - wd) * m; t += NT) {
+            int r = kb + wd + t / m, g = t % m;
+            float2 a = T[(size_t)r * m + g];
+            const float2* Fr = F + (size_t)r * n + kb;
+            for (int l = 0; l < wd; ++l) {
+                float2 L = Fr[l];
+                ffma(a, make_float2(-L.x, -L.y), strip[l * m + g]);
             }
-            __syncthreads();
-            for (int g = threadIdx.x; g < m; g += NT) {
-                for (int j = 1; j < wd; ++j) {
-                    float2 s = XY[(size_t)(kb + j) * w + n + g];
-                    for (int l = 0; l < j; ++l) ffma(s, make_float2(-Ls[j][l].x, -Ls[j][l].y), XY[(size_t)(kb + l) * w + n + g]);
-                    XY[(size_t)(kb + j) * w + n + g] = s;
-                }
-            }
-            __syncthreads();
-            for (int t = threadIdx.x; t < (n - kb - wd) * m; t += NT) {
-                int r = kb + wd + t / m, g = t % m;
-                float2 s = XY[(size_t)r * w + n + g];
-                for (int l = 0; l < wd; ++l) {
-                    float2 L = F[(size_t)r * n + kb + l];
-                    ffma(s, make_float2(-L.x, -L.y), XY[(size_t)(kb + l) * w + n + g]);
-                }
-                XY[(size_t)r * w + n + g] = s;
-            }
-            __syncthreads();
+            T[(size_t)r * m + g] = a;
         }
-        // upper backward solve, 32-row blocks from the bottom
-        const int last = ((n - 1) / PW) * PW;
-        for (int kb = last; kb >= 0; kb -= PW) {
-            const int wd = min(PW, n - kb);
-            for (int t = threadIdx.x; t < PW * PW; t += NT) {
-                int r = t / PW, c = t % PW;
-                Ls[r][c] = (r < wd && c < wd) ? F[(size_t)(kb + r) * n + kb + c] : make_float2(r == c ? 1.f : 0.f, 0.f);
-            }
-            __syncthreads();
-            for (int g = threadIdx.x; g < m; g += NT) {
-                for (int j = wd - 1; j >= 0; --j) {
-                    float2 s = XY[(size_t)(kb + j) * w + n + g];
-                    for (int l = j + 1; l < wd; ++l) ffma(s, make_float2(-Ls[j][l].x, -Ls[j][l].y), XY[(size_t)(kb + l) * w + n + g]);
-                    float2 d = Ls[j][j];
-                    if (d.x == 0.f && d.y == 0.f) d = make_float2(1.f, 0.f);
-                    XY[(size_t)(kb + j) * w + n + g] = fdiv(s, d);
-                }
-            }
-            __syncthreads();
-            for (int t = threadIdx.x; t < kb * m; t += NT) {
-                int r = t / m, g = t % m;
-                float2 s = XY[(size_t)r * w + n + g];
-                for (int l = 0; l < wd; ++l) {
-                    float2 U = F[(size_t)r * n + kb + l];
-                    ffma(s, make_float2(-U.x, -U.y), XY[(size_t)(kb + l) * w + n + g]);
-                }
-                XY[(size_t)r * w + n + g] = s;
-            }
-            __syncthreads();
-        }
+        __syncthreads();
     }
-    // backward over nodes: d_i = w_i - X_i d_{i+1}
-    for (int i = N - 2; i >= 0; --i) {
-        float2* XY = S.XY + e * S.sXY + (size_t)i * n * w;
-        const float2* XYn = S.XY + e * S.sXY + (size_t)(i + 1) * n * w;
-        for (int t = threadIdx.x; t < n * m; t += NT) {
+    // backward, upper with diagonal
+    for (int kb = ((n - 1) / PW) * PW; kb >= 0; kb -= PW) {
+        const int wd = min(PW, n - kb);
+        for (int t = threadIdx.x; t < PW * PW; t += NT) {
+            int r = t / PW, c = t % PW;
+            Ld[r * (PW + 1) + c] = (r < wd && c < wd) ? F[(size_t)(kb + r) * n + kb + c] : make_float2(r == c ? 1.f : 0.f, 0.f);
+        }
+        for (int t = threadIdx.x; t < wd * m; t += NT) strip[t] = T[(size_t)(kb + t / m) * m + t % m];
+        __syncthreads();
+        for (int g = threadIdx.x; g < m; g += NT)
+            for (int j = wd - 1; j >= 0; --j) {
+                float2 a = strip[j * m + g];
+                for (int l = j + 1; l < wd; ++l) {
+                    float2 U = Ld[j * (PW + 1) + l];
+                    ffma(a, make_float2(-U.x, -U.y), strip[l * m + g]);
+                }
+                float2 d = Ld[j * (PW + 1) + j];
+                if (d.x == 0.f && d.y == 0.f) d = make_float2(1.f, 0.f);
+                strip[j * m + g] = fdiv(a, d);
+            }
+        __syncthreads();
+        for (int t = threadIdx.x; t < wd * m; t += NT) T[(size_t)(kb + t / m) * m + t % m] = strip[t];
+        for (int t = threadIdx.x; t < kb * m; t += NT) {
             int r = t / m, g = t % m;
-            float2 s = XY[(size_t)r * w + n + g];
-            for (int k = 0; k < n; ++k) {
-                float2 X = XY[(size_t)r * w + k];
-                ffma(s, make_float2(-X.x, -X.y), XYn[(size_t)k * w + n + g]);
+            float2 a = T[(size_t)r * m + g];
+            const float2* Fr = F + (size_t)r * n + kb;
+            for (int l = 0; l < wd; ++l) {
+                float2 U = Fr[l];
+                ffma(a, make_float2(-U.x, -U.y), strip[l * m + g]);
             }
-            XY[(size_t)r * w + n + g] = s;
+            T[(size_t)r * m + g] = a;
         }
         __syncthreads();
     }
-    // c += d
-    for (size_t t = threadIdx.x; t < (size_t)N * n * m; t += NT) {
+    for (int t = threadIdx.x; t < n * m; t += NT) W[(size_t)(t / m) * w + t % m] = T[t];
+}
+
+// c += d (FP64), active energies
+__global__ void k_mx_update(MixSys S, const int* __restrict__ active) {
+    const int e = blockIdx.y;
+    if (!active[e]) return;
+    const int n = S.n, N = S.N, m = S.m, w = S.w;
+    const size_t tot = (size_t)N * n * m;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
         size_t i = t / ((size_t)n * m), rem = t % ((size_t)n * m);
         int r = (int)(rem / m), g = (int)(rem % m);
         float2 d = S.XY[e * S.sXY + i * n * w + (size_t)r * w + n + g];
-        double2& c = S.C64[e * S.sC + i * n * S.m + (size_t)r * S.m + g];
+        double2& c = S.C64[e * S.sC + t];
         c.x += d.x;
         c.y += d.y;
     }
@@ -385,8 +398,8 @@ __global__ void k_or_status(const SweepJob* __restrict__ jobs, const int* __rest
 
 size_t mixed_bytes_per_energy(int n, int N, int m) {
     // F + XY (complex64) + pivots + L scratch + FP64 solution and residual
-    return sizeof(float2) * ((size_t)N * n * n + (size_t)N * n * (n + m) + (size_t)n * n) + sizeof(int) * (size_t)N * n +
-           2 * sizeof(double2) * (size_t)N * n * m;
+    return sizeof(float2) * ((size_t)N * n * n + (size_t)N * n * (n + m) + (size_t)n * std::max(n, m)) + sizeof(int) * (size_t)N * n +
+           3 * sizeof(double2) * (size_t)N * n * m;   // FP64 solution, residual, float-float copy
 }
 
 int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJob>& jobs, SweepJob* jobs_d, std::vector<ResJob>& res,
@@ -408,7 +421,7 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
     S.sF = (long long)N * n * n;
     S.sP = (long long)N * n;
     S.sXY = (long long)N * n * w;
-    S.sL = (long long)n * n;
+    S.sL = (long long)n * std::max(n, m);   // L_i (n x n), reused as the n x m correction scratch
     S.sC = (long long)N * n * m;
     const size_t bytes = mixed_bytes_per_energy(n, N, m) * nb + 1024 * 4;
     PWQT_TRY(ensure(c, c->ws_mixed, bytes));
@@ -420,6 +433,10 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
     S.piv = (int*)take(sizeof(int) * S.sP * nb);
     S.C64 = (double2*)take(sizeof(double2) * S.sC * nb);
     S.R64 = (double2*)take(sizeof(double2) * S.sC * nb);
+    float4* Cff = (float4*)take(sizeof(float4) * S.sC * nb);
+    PWQT_CUDA(c, cudaMemsetAsync(S.R64, 0, sizeof(double2) * S.sC * nb, st));
+    ResidualFF RF{n, N, c->M0ff.as<float4>(), c->M1ff.as<float4>(), s.HV0ff.as<float4>(), s.HV1ff.as<float4>(), Cff,
+                  (size_t)S.sC};
     S.jobs = jobs_d;
     int* active_d = (int*)take(sizeof(int) * nb);
     int* bits_d = (int*)take(sizeof(int) * nb);
@@ -439,7 +456,7 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
     for (int i = 0; i < N; ++i) {
         float2* Fi = S.F + (size_t)i * n * n;
         float2* XYi = S.XY + (size_t)i * n * w;
-        k_mx_form<<<dim3(fblocks, nb), NT, 0, st>>>(S, i);
+        k_mx_form<<<dim3(fblocks, nb), NT, 0, st>>>(S, i, 0);
         c->launches++;
         if (i > 0) {
             const float2* XYp = S.XY + (size_t)(i - 1) * n * w;
@@ -492,13 +509,16 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         res[b].r_row_stride = m;
     }
     PWQT_CUDA(c, cudaMemcpyAsync(res_d, res.data(), sizeof(ResJob) * nb, cudaMemcpyHostToDevice, st));
+    const size_t lus_smem = ((n * sizeof(int) + 15) / 16) * 16 + sizeof(float2) * (PW * (PW + 1) + (size_t)PW * m);
+    if (lus_smem > 48 * 1024)
+        PWQT_CUDA(c, cudaFuncSetAttribute(k_mx_lusolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lus_smem));
     std::vector<double> resid(nb, 1.0), prev(nb, 1e300);
     std::vector<int> iters(nb, 0), active(nb, 1), stall(nb, 0), bits(nb, 0);
     const double tol = c->opts.ir_tol;
     for (int it = 0;; ++it) {
         PWQT_CUDA(c, cudaMemsetAsync(res[0].rn2, 0, sizeof(double) * 2 * (size_t)nb * m, st));
-        launch_residual_fp64(sys, res_d, nb, st);
-        c->launches += 2;
+        launch_residual_ff(RF, res_d, nb, st);
+        c->launches += 3;
         PWQT_CUDA(c, cudaMemcpyAsync(resid.data(), res[0].resid, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
         PWQT_CUDA(c, cudaStreamSynchronize(st));
         int any = 0;
@@ -518,7 +538,25 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         }
         if (!any) break;
         PWQT_CUDA(c, cudaMemcpyAsync(active_d, active.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
-        k_mx_correct<<<nb, NT, 0, st>>>(S, active_d);
+        for (int i = 0; i < N; ++i) {
+            float2* XYi = S.XY + (size_t)i * n * w;
+            k_mx_load_r<<<dim3(64, nb), NT, 0, st>>>(S, i, active_d);
+            c->launches++;
+            if (i > 0) {
+                k_mx_form<<<dim3(fblocks, nb), NT, 0, st>>>(S, i, 1);
+                const float2* XYp = S.XY + (size_t)(i - 1) * n * w;
+                gemm(S.Lb, S.sL, n, XYp + n, S.sXY, w, XYp + n, S.sXY, w, XYi + n, S.sXY, w, XYi + n, S.sXY, w, m, n, m, n);
+                c->launches++;
+            }
+            k_mx_lusolve<<<nb, NT, lus_smem, st>>>(S, i, active_d);
+            c->launches++;
+        }
+        for (int i = N - 2; i >= 0; --i) {
+            float2* XYi = S.XY + (size_t)i * n * w;
+            const float2* XYn = S.XY + (size_t)(i + 1) * n * w;
+            gemm(XYi, S.sXY, w, XYn + n, S.sXY, w, XYn + n, S.sXY, w, XYi + n, S.sXY, w, XYi + n, S.sXY, w, m, n, m, n);
+        }
+        k_mx_update<<<dim3(256, nb), NT, 0, st>>>(S, active_d);
         c->launches++;
         PWQT_CUDA(c, cudaGetLastError());
     }

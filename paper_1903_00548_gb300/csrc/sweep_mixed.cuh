@@ -27,6 +27,17 @@ struct ResJob {
 };
 
 void launch_residual_fp64(const SweepSys& sys, const ResJob* jobs, int nb, cudaStream_t st);
+// the same residual in float-float arithmetic on the FP32 pipes (~48-bit significand):
+// blocks pre-split into (hi, lo) float pairs, stored as float4 (re_hi, re_lo, im_hi, im_lo)
+struct ResidualFF {
+    int n, N;
+    const float4* M0; const float4* M1;      // n x n
+    const float4* HV0; const float4* HV1;    // N and N-1 blocks
+    float4* Cff; size_t per;                 // float-float copy of the solution, per-energy stride
+};
+void split_ff(const double2* in, float4* out, size_t count, cudaStream_t st);
+void launch_residual_ff(const ResidualFF& R, const ResJob* jobs, int nb, cudaStream_t st);
+void launch_residual_finish(const ResJob* jobs, int nb, cudaStream_t st);
 
 size_t mixed_bytes_per_energy(int n, int N, int m);
 int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJob>& jobs, SweepJob* jobs_d,

@@ -22,8 +22,10 @@ def test_cgemm_matches_fp64_product(pw, shape):
     C = (rng.standard_normal((b, M, N)) + 1j * rng.standard_normal((b, M, N))).astype(np.complex64)
     got = pw.cgemm_c64(A, B, C)
     ref = C.astype(np.complex128) - A.astype(np.complex128) @ B.astype(np.complex128)
-    # 3xTF32 products; the tensor cores' FP32 accumulation truncates, so the error
-    # grows about linearly with K (measured ~K * 2^-24 relative to |A||B| sqrt(K))
+    # 3xTF32 products; the tensor cores' FP32 accumulation truncates, so the kernel
+    # restarts it every 32-complex K stage and sums the stages in FP32 registers:
+    # truncation accrues over at most 24 MMAs (3 x 8 per stage), ~24 * 2^-24.
     scale = np.sqrt(K) * 2.0
     err = np.max(np.abs(got - ref)) / scale
-    assert err < 4.0 * K * 2.0 ** -24 + 1e-6, err
+    print(f"cgemm {shape}: max error / (2 sqrt K) = {err:.2e}")
+    assert err < 4.0 * 24 * 2.0 ** -24 * max(1.0, np.sqrt(K / 32.0)), err
