@@ -173,6 +173,15 @@ def max_over_ranks(world, v):
     return float(t.item())
 
 
+def shard_energies(grid, batch, rank, world):
+    """Energies of one rank's step: `batch` points spread over the grid, interleaved
+    across ranks so that ranks never share an energy while world * batch <= len(grid)."""
+    n = len(grid)
+    stride = max(1, n // (batch * world))
+    idx = (np.arange(batch) * world * stride + rank * stride) % n
+    return np.sort(grid[idx])
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args, world, rank):
     if rank != 0:
@@ -217,8 +226,7 @@ def run_ours(args, world, rank, local):
     prec = pw.MIXED if prec_name == "mixed" else pw.FP64
     batch = args.batch or (152 if prec == pw.FP64 else 64)
     n_grid = len(wl.energies)
-    idx = (np.arange(batch) * max(1, n_grid // batch) + rank * batch) % n_grid
-    E = np.sort(wl.energies[idx])
+    E = shard_energies(wl.energies, batch, rank, world)
 
     oracle_proc = None
     if rank == 0 and not args.no_cpu_baseline:

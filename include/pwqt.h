@@ -58,7 +58,7 @@ typedef struct {
     int    device;             /* CUDA device ordinal                              */
     size_t hbm_budget_bytes;   /* 0: use 90 % of the free device memory            */
     double ir_tol;             /* mixed path: stop when ||B - A c|| <= ir_tol ||B||
-                                  (max over columns); 0 -> 1e-12                    */
+                                  (max over columns); 0 -> 1e-11                    */
     int    ir_max_iters;       /* mixed path refinement limit; 0 -> 40              */
     int    batch;              /* energies per sweep launch; 0 -> from the budget   */
 } pwqt_opts;

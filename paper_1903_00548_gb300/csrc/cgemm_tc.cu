@@ -39,7 +39,7 @@ constexpr uint32_t A_BYTES = BM * BKR * 4;           // 32 KB
 constexpr uint32_t B_BYTES = BNR * BKR * 4;          // 64 KB
 constexpr uint32_t SMEM_BYTES = 2 * A_BYTES + 2 * B_BYTES + 64;
 constexpr uint32_t TMEM_COLS = 256;
-constexpr long long SPIN_LIMIT = 1ll << 24;
+constexpr long long SPIN_LIMIT = 1ll << 22;   // bounded mbarrier polling (each poll returns within microseconds)
 
 __device__ int g_tc_error = 0;
 

@@ -42,7 +42,7 @@ int pwqt_create(pwqt_ctx** out, const pwqt_opts* opts) {
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) { cudaGetLastError(); return PWQT_ERR_NO_DEVICE; }
     auto* c = new pwqt_ctx();
     if (opts) c->opts = *opts;
-    if (c->opts.ir_tol <= 0) c->opts.ir_tol = 1e-12;
+    if (c->opts.ir_tol <= 0) c->opts.ir_tol = 1e-11;
     if (c->opts.ir_max_iters <= 0) c->opts.ir_max_iters = 40;
     c->dev = c->opts.device;
     if (c->dev < 0 || c->dev >= ndev) { delete c; return PWQT_ERR_INVALID_ARG; }

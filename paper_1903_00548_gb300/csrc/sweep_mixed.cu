@@ -529,7 +529,7 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
             else stall[b] = 0;
             if (stall[b] >= 3 || iters[b] >= c->opts.ir_max_iters) {
                 active[b] = 0;
-                bits[b] |= PWQT_ST_IR_NO_CONVERGE;
+                bits[b] |= PWQT_ST_IR_NO_CONVERGE;   // final residual above ir_tol
                 continue;
             }
             prev[b] = std::min(prev[b], resid[b]);
