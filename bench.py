@@ -287,6 +287,7 @@ def run_ours(args, world, rank, local):
     total_ms = ev_s.elapsed_time(ev_e)
     per_step = [a.elapsed_time(b) for a, b in step_ms]
     launches = (ctx.kernel_launches() - launches0) // max(1, args.steps)
+    ir_res_ms, ir_cor_ms, ir_iters = ctx.profile_refinement()
     sweep_ms, sweep_n, sweep_flops = ctx.profile(False)
     total_ms = max_over_ranks(world, total_ms)
     value = world * batch * args.steps / (total_ms / 1e3)
@@ -308,6 +309,25 @@ def run_ours(args, world, rank, local):
     e2e_value = world * batch * e2e_steps / t_e2e
     h2d = 8 * batch
     d2h = batch * (8 * 4 + 4 * 4 + 8 * 2 * N)
+
+    # density-matrix route (reported apart from the energy-solve metric): one more
+    # solve of the same energies with the rank-m accumulation, then n(r) on a grid
+    dens = None
+    if not args.no_density:
+        w = np.full(len(E), (wl.energies[1] - wl.energies[0]) if len(wl.energies) > 1 else 1.0)
+        mu = float(np.median(E))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        ctx.accumulate_density(0, E, w, mu, mu - 0.1, 0.025852, prec)
+        t_acc = time.perf_counter() - t0
+        nx, nz = 64, 16
+        t0 = time.perf_counter()
+        grid = ctx.density_grid(0, nx, nz)
+        t_grid = time.perf_counter() - t0
+        t_solve = (total_ms / args.steps) / 1e3
+        dens = {"accumulate_s_per_energy": max(t_acc - t_solve, 0.0) / len(E),
+                "solve_plus_accumulate_s": t_acc, "grid_s": t_grid, "grid": [nx, nz],
+                "grid_points": int(grid.size), "n_max": float(grid.max())}
 
     # roofline of the dominant kernel (the block sweep)
     bf16, hbm, src = peaks()
@@ -332,7 +352,11 @@ def run_ours(args, world, rank, local):
             "latency_ms": {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99)),
                            "unit": f"per step of {batch} energies"},
             "sigma_cold_s_per_energy": t_leads / max(1, len(set(E.tolist()))), "setup_s": t_setup,
-            "gpu_launches": int(launches), "clocks": clk, "roofline": roof,
+            "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "density": dens,
+            "phases_ms_per_step": {"sweep": sweep_ms / args.steps, "refine_residual": ir_res_ms / args.steps,
+                                   "refine_correction": ir_cor_ms / args.steps,
+                                   "refine_iterations": ir_iters / args.steps,
+                                   "note": "CUDA events; profiling serialises the host with each phase"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "results": {"max_resid": float(np.max(resid)), "max_iters": int(np.max(iters)),
                         "status_nonzero": int(np.count_nonzero(status)), "mean_modes": float(nopen.sum(1).mean()),
@@ -364,6 +388,7 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--nodes", type=int, default=0, help="development only: shorter device")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-density", action="store_true", help="skip the density-matrix timing")
     args = ap.parse_args(argv)
     world, rank, local = dist_setup()
     if args.impl == "reference":

@@ -199,6 +199,15 @@ int pwqt_profile(pwqt_ctx* ctx, int enable, double* sweep_ms, long long* sweep_l
                  double* sweep_flops, int reset);
 
 /*
+ * Refinement phases of the mixed path recorded while pwqt_profile is enabled
+ * (same reset): total milliseconds of the residual evaluations (float-float
+ * B - A c, Sec. 3.2 system) and of the correction solves with the stored
+ * complex64 factors, and the number of batched refinement iterations.  Any
+ * pointer may be NULL.
+ */
+int pwqt_profile_refinement(pwqt_ctx* ctx, double* residual_ms, double* correction_ms, long long* iterations);
+
+/*
  * pwqt_solve_noalloc -- the FP64 solve without any device allocation.
  * The paper has no counterpart; this entry point exists for callers that cannot
  * call cudaMalloc while they solve: code embedded in a host program that owns the
@@ -235,6 +244,53 @@ int pwqt_solve_noalloc(pwqt_ctx* ctx, int sys, int n_E, const double* E, double*
  */
 int pwqt_cgemm_c64(int batch, int M, int N, int K, const float* A, int lda, const float* B, int ldb,
                    float* C, int ldc);
+
+/*
+ * Density-matrix route to the electron density (Sec. 3.3, Eq. density_matrices
+ * and Eq. density_3d_fast).  Each system keeps, on the device, the density-matrix
+ * blocks that the density needs: rho_d[a] (node a with itself, N blocks) and
+ * rho_u[a] (node a with node a+1, N-1 blocks), n x n complex128 each,
+ *     rho_d[a]_{alpha beta} = sum_{E, gamma} w_E g_gamma f_gamma conj(c_{a alpha}) c_{a beta}
+ *     rho_u[a]_{alpha beta} = sum_{E, gamma} w_E g_gamma f_gamma conj(c_{a alpha}) c_{a+1 beta}
+ * over the injected modes gamma of every accumulated energy, g = 2/|dE/dk| and
+ * f = f_FD(E - mu_s) for source-injected modes, f_FD(E - mu_d) for drain-injected
+ * ones, f_FD(x) = 1/(1 + e^{x/kT}) (a step for kT = 0).  pwqt_set_extrinsic
+ * discards a system's density.
+ *
+ * pwqt_density_reset: zero (allocating on first use, 2 N n^2 complex128) the
+ * density of system `sys`.  Errors: PWQT_ERR_STATE (unknown system), PWQT_ERR_OOM.
+ */
+int pwqt_density_reset(pwqt_ctx* ctx, int sys);
+
+/*
+ * Solve system `sys` at the n_E energies E (host) exactly as pwqt_solve with
+ * `precision`, and add each solution's rank-m contribution to the system's
+ * density (FP64 kernels); w (host, n_E) are the energy quadrature weights.  The
+ * first call after pwqt_set_extrinsic starts from zero.  status (host, n_E, may
+ * be NULL) receives the PWQT_ST_* bits of each energy; energies whose contacts
+ * fail the mode count contribute nothing.  Errors: as pwqt_solve, and
+ * PWQT_ERR_INVALID_ARG for NULL E / w, a non-finite weight or mu, or kT < 0.
+ */
+int pwqt_accumulate_density(pwqt_ctx* ctx, int sys, int n_E, const double* E, const double* w,
+                            double mu_s, double mu_d, double kT, int precision, int* status);
+
+/*
+ * Copy the density matrix of system `sys` to the host: rho_d (N x n x n complex)
+ * and rho_u ((N-1) x n x n complex), row-major interleaved; either may be NULL.
+ * Errors: PWQT_ERR_STATE if nothing has been accumulated since pwqt_set_extrinsic.
+ */
+int pwqt_get_density_matrix(pwqt_ctx* ctx, int sys, double* rho_d, double* rho_u);
+
+/*
+ * Electron density n(r) on a real-space grid from the accumulated density
+ * matrix (Eq. density_3d_fast).  On the element between nodes e and e+1
+ * (e < N-1) the grid points are x_j = j Lx / nx (j < nx; only x = 0 for a
+ * dim == 1 cell) and z = z_e + (q + 1/2) Lz / nz (q < nz).  n_r (host) receives
+ * (N-1) x nx_eff x nz doubles, index (e * nx_eff + j) * nz + q, nx_eff = nx
+ * (dim 2) or 1 (dim 1).  1 <= nx, nz <= 4096.  Errors: PWQT_ERR_STATE (no
+ * density yet), PWQT_ERR_INVALID_ARG, PWQT_ERR_OOM.
+ */
+int pwqt_density_grid(pwqt_ctx* ctx, int sys, int nx, int nz, double* n_r);
 
 /* Launch counters of the library's own kernels since the last reset. */
 int pwqt_kernel_launches(pwqt_ctx* ctx, long long* count, int reset);

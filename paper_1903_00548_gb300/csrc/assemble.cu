@@ -388,6 +388,13 @@ int assemble_from_basis(pwqt_ctx* c, const pwqt_cell* cell, int n_bands, const d
     c->n_bands = nb;
     c->Lz = cell->Lz;
     c->Lx = cell->Lx;
+    c->dim = cell->dim;
+    for (int g = 0; g < 2; ++g) {   // kept for evaluating the basis on a real-space grid
+        c->pw_n[g] = n_pw[g];
+        c->pw_mx[g] = std::move(dmx[g]);
+        c->pw_mz[g] = std::move(dmz[g]);
+        c->pw_C[g] = std::move(Cs[g]);
+    }
     c->eps.assign(eps_host, eps_host + n);
     c->systems.clear();
     c->cache.clear();

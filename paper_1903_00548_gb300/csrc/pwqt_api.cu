@@ -20,7 +20,8 @@ __global__ void k_bands_hk(int n, double2 ph, const double2* H0, const double2* 
     Mk[(size_t)c * n + r] = cadd(M0[rm], cadd(cmul(M1[rm], ph), cmul(cconj(M1[tm]), iph)));
 }
 
-int solve_common(pwqt_ctx* c, int sys, int n_E, const double* E, int precision, SolveOut& dev, cudaStream_t st) {
+int solve_common(pwqt_ctx* c, int sys, int n_E, const double* E, int precision, SolveOut& dev, cudaStream_t st,
+                 const DensityAcc* dens = nullptr) {
     if (!c->n) return fail(c, PWQT_ERR_STATE, "no basis: call pwqt_assemble_intrinsic first");
     auto it = c->systems.find(sys);
     if (it == c->systems.end()) return fail(c, PWQT_ERR_STATE, "unknown system: call pwqt_set_extrinsic first");
@@ -29,7 +30,7 @@ int solve_common(pwqt_ctx* c, int sys, int n_E, const double* E, int precision, 
     if (c->n > 1024) return fail(c, PWQT_ERR_INVALID_ARG, "block size above 1024");
     for (int e = 0; e < n_E; ++e)
         if (!std::isfinite(E[e])) return fail(c, PWQT_ERR_INVALID_ARG, "non-finite energy");
-    return solve_batch(c, it->second, n_E, E, precision, dev, st);
+    return solve_batch(c, it->second, n_E, E, precision, dev, st, dens);
 }
 }  // namespace
 
@@ -74,6 +75,8 @@ int pwqt_destroy(pwqt_ctx* c) {
     if (c->stream) cudaStreamDestroy(c->stream);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->ev2) cudaEventDestroy(c->ev2);
+    if (c->ev3) cudaEventDestroy(c->ev3);
     delete c;
     return PWQT_OK;
 }
@@ -133,6 +136,9 @@ int pwqt_set_extrinsic(pwqt_ctx* c, int sys, int n_nodes, const double* U) {
     s.U.assign(U, U + n_nodes);
     s.Us = U[0];
     s.Ud = U[n_nodes - 1];
+    s.rho_d.release();   // a new potential starts a new density
+    s.rho_u.release();
+    s.rho_energies = 0;
     int r = build_system_blocks(c, s);
     if (r != PWQT_OK) c->systems.erase(sys);
     return r;
@@ -252,12 +258,17 @@ int pwqt_profile(pwqt_ctx* c, int enable, double* sweep_ms, long long* sweep_lau
     if (enable && !c->ev0) {
         PWQT_CUDA(c, cudaEventCreate(&c->ev0));
         PWQT_CUDA(c, cudaEventCreate(&c->ev1));
+        PWQT_CUDA(c, cudaEventCreate(&c->ev2));
+        PWQT_CUDA(c, cudaEventCreate(&c->ev3));
     }
     c->profile = enable;
     if (sweep_ms) *sweep_ms = c->prof_ms;
     if (sweep_launches) *sweep_launches = c->prof_launches;
     if (sweep_flops) *sweep_flops = c->prof_flops;
-    if (reset) { c->prof_ms = 0; c->prof_launches = 0; c->prof_flops = 0; }
+    if (reset) {
+        c->prof_ms = 0; c->prof_launches = 0; c->prof_flops = 0;
+        c->prof_phase_ms[0] = c->prof_phase_ms[1] = 0; c->prof_ir_iters = 0;
+    }
     return PWQT_OK;
 }
 
@@ -265,6 +276,93 @@ int pwqt_kernel_launches(pwqt_ctx* c, long long* count, int reset) {
     PWQT_TRY(check_ctx(c));
     if (count) *count = c->launches;
     if (reset) c->launches = 0;
+    return PWQT_OK;
+}
+
+
+int pwqt_density_reset(pwqt_ctx* c, int sys) {
+    PWQT_TRY(check_ctx(c));
+    auto it = c->systems.find(sys);
+    if (it == c->systems.end()) return fail(c, PWQT_ERR_STATE, "unknown system: call pwqt_set_extrinsic first");
+    cudaSetDevice(c->dev);
+    PWQT_TRY(density_reset(c, it->second, c->stream));
+    PWQT_CUDA(c, cudaStreamSynchronize(c->stream));
+    return PWQT_OK;
+}
+
+int pwqt_accumulate_density(pwqt_ctx* c, int sys, int n_E, const double* E, const double* w, double mu_s, double mu_d, double kT,
+                            int precision, int* status) {
+    PWQT_TRY(check_ctx(c));
+    auto it = c->systems.find(sys);
+    if (it == c->systems.end()) return fail(c, PWQT_ERR_STATE, "unknown system: call pwqt_set_extrinsic first");
+    if (n_E < 0 || (n_E > 0 && (!E || !w))) return fail(c, PWQT_ERR_INVALID_ARG, "energies and weights are required");
+    if (!std::isfinite(mu_s) || !std::isfinite(mu_d) || !std::isfinite(kT) || kT < 0)
+        return fail(c, PWQT_ERR_INVALID_ARG, "mu_s, mu_d must be finite and kT >= 0");
+    for (int e = 0; e < n_E; ++e)
+        if (!std::isfinite(w[e])) return fail(c, PWQT_ERR_INVALID_ARG, "non-finite weight");
+    cudaSetDevice(c->dev);
+    System& s = it->second;
+    if (!s.rho_d.p) PWQT_TRY(density_reset(c, s, c->stream));
+    if (n_E == 0) return PWQT_OK;
+    const int N = s.N;
+    const size_t ne = (size_t)n_E;
+    DBuf out;
+    PWQT_TRY(alloc(c, out, sizeof(double) * ne * (4 + 2 * (size_t)N) + sizeof(int) * ne * 4 + 2048));
+    char* p = out.as<char>();
+    auto take = [&](size_t b) { char* q = p; p += (b + 255) / 256 * 256; return q; };
+    SolveOut o;
+    o.T = (double*)take(sizeof(double) * ne);
+    o.R = (double*)take(sizeof(double) * ne);
+    o.T_ds = (double*)take(sizeof(double) * ne);
+    o.resid = (double*)take(sizeof(double) * ne);
+    o.node_n = (double*)take(sizeof(double) * ne * 2 * N);
+    o.n_open = (int*)take(sizeof(int) * ne * 2);
+    o.iters = (int*)take(sizeof(int) * ne);
+    o.status = (int*)take(sizeof(int) * ne);
+    DensityAcc d{w, mu_s, mu_d, kT};
+    PWQT_TRY(solve_common(c, sys, n_E, E, precision, o, c->stream, &d));
+    PWQT_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (status) PWQT_CUDA(c, cudaMemcpy(status, o.status, sizeof(int) * ne, cudaMemcpyDeviceToHost));
+    return PWQT_OK;
+}
+
+int pwqt_get_density_matrix(pwqt_ctx* c, int sys, double* rho_d, double* rho_u) {
+    PWQT_TRY(check_ctx(c));
+    auto it = c->systems.find(sys);
+    if (it == c->systems.end()) return fail(c, PWQT_ERR_STATE, "unknown system: call pwqt_set_extrinsic first");
+    System& s = it->second;
+    if (!s.rho_d.p) return fail(c, PWQT_ERR_STATE, "no density accumulated: call pwqt_accumulate_density first");
+    cudaSetDevice(c->dev);
+    const size_t nn = (size_t)c->n * c->n;
+    if (rho_d) PWQT_CUDA(c, cudaMemcpy(rho_d, s.rho_d.p, sizeof(double2) * nn * s.N, cudaMemcpyDeviceToHost));
+    if (rho_u && s.N > 1) PWQT_CUDA(c, cudaMemcpy(rho_u, s.rho_u.p, sizeof(double2) * nn * (s.N - 1), cudaMemcpyDeviceToHost));
+    return PWQT_OK;
+}
+
+int pwqt_density_grid(pwqt_ctx* c, int sys, int nx, int nz, double* n_r) {
+    PWQT_TRY(check_ctx(c));
+    auto it = c->systems.find(sys);
+    if (it == c->systems.end()) return fail(c, PWQT_ERR_STATE, "unknown system: call pwqt_set_extrinsic first");
+    System& s = it->second;
+    if (!s.rho_d.p) return fail(c, PWQT_ERR_STATE, "no density accumulated: call pwqt_accumulate_density first");
+    if (nx < 1 || nz < 1 || nx > 4096 || nz > 4096 || !n_r) return fail(c, PWQT_ERR_INVALID_ARG, "1 <= nx, nz <= 4096 and n_r required");
+    cudaSetDevice(c->dev);
+    const int nxe = c->dim == 2 ? nx : 1;
+    const size_t count = (size_t)std::max(s.N - 1, 0) * nxe * nz;
+    if (count == 0) return PWQT_OK;
+    DBuf out;
+    PWQT_TRY(alloc(c, out, sizeof(double) * count));
+    PWQT_TRY(density_grid(c, s, nx, nz, out.as<double>(), c->stream));
+    PWQT_CUDA(c, cudaMemcpy(n_r, out.p, sizeof(double) * count, cudaMemcpyDeviceToHost));
+    return PWQT_OK;
+}
+
+
+int pwqt_profile_refinement(pwqt_ctx* c, double* residual_ms, double* correction_ms, long long* iterations) {
+    PWQT_TRY(check_ctx(c));
+    if (residual_ms) *residual_ms = c->prof_phase_ms[0];
+    if (correction_ms) *correction_ms = c->prof_phase_ms[1];
+    if (iterations) *iterations = c->prof_ir_iters;
     return PWQT_OK;
 }
 

@@ -96,6 +96,26 @@ struct System {
     DBuf HV0, HV1;        // N and N-1 blocks: H_ii + V_ii, H_{i,i+1} + V_{i,i+1} (complex128)
     DBuf HV0f, HV1f;      // complex64 copies (mixed path)
     DBuf HV0ff, HV1ff;    // float-float splits (refinement residual)
+    // density matrix of Sec. 3.3: N diagonal blocks and N-1 blocks (a, a+1), n x n complex128
+    DBuf rho_d, rho_u;
+    long long rho_energies = 0;   // energies accumulated since the last reset
+};
+
+// Density-matrix accumulation requested alongside a solve (Sec. 3.3)
+struct DensityAcc {
+    const double* w;              // host, quadrature weight per energy of the call
+    double mu_s, mu_d, kT;        // contact electrochemical potentials, temperature (eV)
+};
+
+// one solved energy as seen by the accumulation kernel
+struct DensJob {
+    const double2* C;             // c: node i at C + i*node_stride, row r at + r*row_stride
+    size_t node_stride;
+    int row_stride;
+    int ms, md;
+    const double* v_in_s;         // |dE/dk| of the injected modes
+    const double* v_in_d;
+    double scale_s, scale_d;      // w_E f_FD(E - mu_s), w_E f_FD(E - mu_d)
 };
 
 }  // namespace pwqt
@@ -113,6 +133,11 @@ struct pwqt_ctx {
     // basis
     int n = 0, n_bands = 0;
     double Lz = 0, Lx = 0;
+    int dim = 1;
+    // plane-wave expansion of the Bloch waves per k group (0: k = 0, 1: k = pi/Lz),
+    // rows sorted by (mx, mz): mx, mz (int) and coefficients (n_pw x n_bands complex128)
+    int pw_n[2] = {0, 0};
+    pwqt::DBuf pw_mx[2], pw_mz[2], pw_C[2];
     std::vector<double> eps;               // 2 n_bands
     pwqt::DBuf H0, H1, M0, M1, W;          // n x n row-major complex128; W: 6 blocks
     pwqt::DBuf M0f, M1f, H0f, H1f;         // complex64 copies
@@ -122,7 +147,7 @@ struct pwqt_ctx {
     // scratch reused across calls
     pwqt::DBuf work_a, work_b;
     // grow-only workspaces of the sweep (kept across calls: no allocation in steady state)
-    pwqt::DBuf ws_xy, ws_s, ws_norms, ws_jobs, ws_obs, ws_res, ws_mixed;
+    pwqt::DBuf ws_xy, ws_s, ws_norms, ws_jobs, ws_obs, ws_res, ws_mixed, ws_dens;
     pwqt::DBuf zero_nn;   // n x n zeros
     // optional CUDA-event timing of the dominant (block-sweep) kernels
     int profile = 0;
@@ -130,6 +155,10 @@ struct pwqt_ctx {
     long long prof_launches = 0;
     double prof_flops = 0.0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // refinement phases of the mixed path: [0] residuals, [1] corrections; iterations
+    double prof_phase_ms[2] = {0.0, 0.0};
+    long long prof_ir_iters = 0;
+    cudaEvent_t ev2 = nullptr, ev3 = nullptr;
     // host threads that fill the contact cache concurrently
     int lead_threads = 8;
     std::vector<std::unique_ptr<pwqt::LeadWorker>> workers;
@@ -167,7 +196,12 @@ struct SolveOut {
     int *n_open, *iters, *status;
 };
 int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E_host, int precision,
-                const SolveOut& dev_out, cudaStream_t st);
+                const SolveOut& dev_out, cudaStream_t st, const DensityAcc* dens = nullptr);
+
+// density (density.cu)
+int density_alloc(pwqt_ctx* c, System& s);
+int density_reset(pwqt_ctx* c, System& s, cudaStream_t st);
+int density_grid(pwqt_ctx* c, System& s, int nx, int nz, double* out_dev, cudaStream_t st);
 
 // small kernels (util.cu)
 void transpose_c128(const double2* in, double2* out, int rows, int cols, cudaStream_t st);

@@ -21,16 +21,26 @@ __device__ __forceinline__ ff split(double x) {
 }
 // acc += a * b (all float-float), accumulation without renormalising every step
 __device__ __forceinline__ void ff_fma(ff& acc, ff a, ff b) {
-    float p = a.hi * b.hi;
+    // __fmul_rn / __fadd_rn keep the compiler from contracting the product into the
+    // two-sum below, which would break its exactness
+    float p = __fmul_rn(a.hi, b.hi);
     float pe = fmaf(a.hi, b.hi, -p);
     pe = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, pe));
-    float s = acc.hi + p;
+    float s = __fadd_rn(acc.hi, p);
     float bb = s - acc.hi;
     float e = (acc.hi - (s - bb)) + (p - bb);
     acc.hi = s;
     acc.lo += e + pe;
 }
 __device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
+// acc -= b, with the rounding error of the leading subtraction kept (two-sum)
+__device__ __forceinline__ void ff_sub(ff& acc, float bhi, float blo) {
+    float s = acc.hi - bhi;
+    float bb = s - acc.hi;
+    float e = (acc.hi - (s - bb)) - (bhi + bb);
+    acc.hi = s;
+    acc.lo += e - blo;
+}
 __device__ __forceinline__ double ff_d(ff a) { return (double)a.hi + (double)a.lo; }
 
 constexpr int COLS = 4;    // solution columns per thread
@@ -53,8 +63,8 @@ __device__ __forceinline__ cff form(ff E, float4 mm, float4 hh) {
     cff r{{0.f, 0.f}, {0.f, 0.f}};
     ff_fma(r.re, E, ff{mm.x, mm.y});
     ff_fma(r.im, E, ff{mm.z, mm.w});
-    r.re.hi -= hh.x; r.re.lo -= hh.y;
-    r.im.hi -= hh.z; r.im.lo -= hh.w;
+    ff_sub(r.re, hh.x, hh.y);
+    ff_sub(r.im, hh.z, hh.w);
     return r;
 }
 
@@ -80,67 +90,111 @@ __global__ void k_split_solution(const ResJob* __restrict__ jobs, int N, int n, 
     }
 }
 
-constexpr int RCOLS = 8;
+// Tiled residual: one CTA computes a 64-row x 32-column tile of r_i = b_i - [L_i D_i U_i] [c_{i-1}; c_i; c_{i+1}]
+// for one node i of one energy.  The K dimension (3n: the three blocks of the row) runs in chunks of 32: the
+// block elements E M - H (and -Sigma at the end nodes) are formed in float-float while they are staged in
+// shared memory, the solution chunk is staged beside them, and every thread accumulates a 4 x 2 micro-tile.
+constexpr int RT = 64;    // rows per CTA
+constexpr int CT = 32;    // columns per CTA
+constexpr int KC = 32;    // K chunk
 
-__global__ void __launch_bounds__(256) k_residual_ff(ResidualFF R, const ResJob* __restrict__ jobs) {
-    const ResJob J = jobs[blockIdx.y];
+__global__ void __launch_bounds__(256) k_residual_ff(ResidualFF R, const ResJob* __restrict__ jobs, int col_tiles) {
+    extern __shared__ float4 rsm[];
+    float4 (*As)[KC + 1] = reinterpret_cast<float4 (*)[KC + 1]>(rsm);          // [RT][KC + 1]
+    float4 (*Cs)[CT] = reinterpret_cast<float4 (*)[CT]>(rsm + RT * (KC + 1));   // [KC][CT]
+    __shared__ double rsum[CT], bsum[CT];
+    const ResJob J = jobs[blockIdx.z];
     const int n = R.n, N = R.N, m = J.ms + J.md;
-    const int i = blockIdx.x;
-    if (m == 0) return;
-    const double2 Ed = make_double2(J.E, 0.0);
-    const ff E = split(Ed.x);
-    const float4* cs = R.Cff + R.per * blockIdx.y;
-    const float4* ci = cs + (size_t)i * J.node_stride;
-    const float4* cm1 = i > 0 ? cs + (size_t)(i - 1) * J.node_stride : nullptr;
-    const float4* cp1 = i < N - 1 ? cs + (size_t)(i + 1) * J.node_stride : nullptr;
-    const float4* HV0 = R.HV0 + (size_t)i * n * n;
-    const float4* HV1 = R.HV1 + (size_t)i * n * n;
-    const float4* HVm = i > 0 ? R.HV1 + (size_t)(i - 1) * n * n : nullptr;
-    const int groups = (m + RCOLS - 1) / RCOLS;
-    for (int t = threadIdx.x; t < n * groups; t += blockDim.x) {
-        const int r = t / groups, g0 = (t % groups) * RCOLS;
-        cff acc[RCOLS];
+    const int i = blockIdx.y;
+    const int r0 = (blockIdx.x / col_tiles) * RT, c0 = (blockIdx.x % col_tiles) * CT;
+    if (c0 >= m) return;
+    const int t = threadIdx.x, tx = t % 16, ty = t / 16;
+    const ff E = split(J.E);
+    const float4* cs = R.Cff + R.per * blockIdx.z;
+    const double2* sig = nullptr;
+    if (i == 0 && J.sig_s) sig = J.sig_s;
+    if (i == N - 1 && J.sig_d) sig = J.sig_d;
+    const bool both = i == 0 && i == N - 1 && J.sig_s && J.sig_d;
+    if (t < CT) { rsum[t] = 0.0; bsum[t] = 0.0; }
+    cff acc[4][2];
 #pragma unroll
-        for (int q = 0; q < RCOLS; ++q) acc[q] = cff{{0.f, 0.f}, {0.f, 0.f}};
-        for (int k = 0; k < n; ++k) {
-            const size_t rk = (size_t)r * n + k;
-            cff D = form(E, R.M0[rk], HV0[rk]);
-            if ((i == 0 && J.sig_s) || (i == N - 1 && J.sig_d)) {   // end blocks: subtract Sigma (FP64, two nodes only)
-                double2 sg = i == 0 ? J.sig_s[rk] : J.sig_d[rk];
-                if (i == 0 && i == N - 1) sg = cadd(J.sig_s[rk], J.sig_d[rk]);
-                ff a = split(sg.x), b = split(sg.y);
-                D.re.hi -= a.hi; D.re.lo -= a.lo; D.im.hi -= b.hi; D.im.lo -= b.lo;
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) acc[a][b] = cff{{0.f, 0.f}, {0.f, 0.f}};
+    // blk 0: L_i = (E M1 - HV1_{i-1})^H with c_{i-1}; blk 1: D_i with c_i; blk 2: U_i with c_{i+1}
+    for (int blk = 0; blk < 3; ++blk) {
+        if ((blk == 0 && i == 0) || (blk == 2 && i == N - 1)) continue;
+        const float4* cn = cs + (size_t)(i + blk - 1) * J.node_stride;
+        const float4* Mb = blk == 1 ? R.M0 : R.M1;
+        const float4* Hb = blk == 1 ? R.HV0 + (size_t)i * n * n : R.HV1 + (size_t)(blk == 0 ? i - 1 : i) * n * n;
+        for (int k0 = 0; k0 < n; k0 += KC) {
+            // stage the formed block elements
+            for (int e = t; e < RT * KC; e += 256) {
+                int r, k;
+                if (blk == 0) { r = e % RT; k = e / RT; }   // transposed source: consecutive threads along r
+                else { r = e / KC; k = e % KC; }
+                const int gr = r0 + r, gk = k0 + k;
+                cff v{{0.f, 0.f}, {0.f, 0.f}};
+                if (gr < n && gk < n) {
+                    if (blk == 0) {
+                        const size_t kr = (size_t)gk * n + gr;
+                        v = form(E, Mb[kr], Hb[kr]);
+                        v.im.hi = -v.im.hi;
+                        v.im.lo = -v.im.lo;
+                    } else {
+                        const size_t rk = (size_t)gr * n + gk;
+                        v = form(E, Mb[rk], Hb[rk]);
+                        if (blk == 1 && sig) {
+                            double2 sg = sig[rk];
+                            if (both) sg = cadd(J.sig_s[rk], J.sig_d[rk]);
+                            const ff a = split(sg.x), b = split(sg.y);
+                            ff_sub(v.re, a.hi, a.lo);
+                            ff_sub(v.im, b.hi, b.lo);
+                        }
+                    }
+                }
+                As[r][k] = make_float4(v.re.hi, v.re.lo, v.im.hi, v.im.lo);
             }
-#pragma unroll
-            for (int q = 0; q < RCOLS; ++q)
-                if (g0 + q < m) cmac(acc[q], D, c4(ci[(size_t)k * J.row_stride + g0 + q]));
-            if (cp1) {
-                const cff U = form(E, R.M1[rk], HV1[rk]);
-#pragma unroll
-                for (int q = 0; q < RCOLS; ++q)
-                    if (g0 + q < m) cmac(acc[q], U, c4(cp1[(size_t)k * J.row_stride + g0 + q]));
+            // stage the solution chunk
+            for (int e = t; e < KC * CT; e += 256) {
+                const int k = e / CT, cc = e % CT, gk = k0 + k, gc = c0 + cc;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (gk < n && gc < m) v = cn[(size_t)gk * J.row_stride + gc];
+                Cs[k][cc] = v;
             }
-            if (cm1) {
-                const size_t kr = (size_t)k * n + r;
-                cff L = form(E, R.M1[kr], HVm[kr]);
-                L.im.hi = -L.im.hi; L.im.lo = -L.im.lo;   // conjugate transpose of U_{i-1}
+            __syncthreads();
+#pragma unroll 2
+            for (int k = 0; k < KC; ++k) {
+                const cff x0 = c4(Cs[k][tx]), x1 = c4(Cs[k][tx + 16]);
 #pragma unroll
-                for (int q = 0; q < RCOLS; ++q)
-                    if (g0 + q < m) cmac(acc[q], L, c4(cm1[(size_t)k * J.row_stride + g0 + q]));
+                for (int a = 0; a < 4; ++a) {
+                    const cff d = c4(As[ty + 16 * a][k]);
+                    cmac(acc[a][0], d, x0);
+                    cmac(acc[a][1], d, x1);
+                }
             }
+            __syncthreads();
         }
+    }
+    // epilogue: r = b - A c in FP64, column norms reduced in the CTA first
 #pragma unroll
-        for (int q = 0; q < RCOLS; ++q) {
-            const int g = g0 + q;
-            if (g >= m) continue;
-            double2 b = make_double2(0, 0);
-            if (i == 0 && g < J.ms) b = J.rhs_s[(size_t)r * J.ms + g];
-            if (i == N - 1 && g >= J.ms) b = J.rhs_d[(size_t)r * J.md + (g - J.ms)];
-            double2 res = make_double2(b.x - ff_d(acc[q].re), b.y - ff_d(acc[q].im));
-            if (J.Rout) J.Rout[(size_t)i * J.r_node_stride + (size_t)r * J.r_row_stride + g] = res;
-            atomicAdd(&J.rn2[g], cnorm2(res));
-            atomicAdd(&J.bn2[g], cnorm2(b));
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int gr = r0 + ty + 16 * a, cc = tx + 16 * b, g = c0 + cc;
+            if (gr >= n || g >= m) continue;
+            double2 bv = make_double2(0, 0);
+            if (i == 0 && g < J.ms) bv = J.rhs_s[(size_t)gr * J.ms + g];
+            if (i == N - 1 && g >= J.ms) bv = J.rhs_d[(size_t)gr * J.md + (g - J.ms)];
+            const double2 res = make_double2(bv.x - ff_d(acc[a][b].re), bv.y - ff_d(acc[a][b].im));
+            if (J.Rout) J.Rout[(size_t)i * J.r_node_stride + (size_t)gr * J.r_row_stride + g] = res;
+            atomicAdd(&rsum[cc], cnorm2(res));
+            if (i == 0 || i == N - 1) atomicAdd(&bsum[cc], cnorm2(bv));
         }
+    __syncthreads();
+    if (t < CT && c0 + t < m) {
+        atomicAdd(&J.rn2[c0 + t], rsum[t]);
+        if (i == 0 || i == N - 1) atomicAdd(&J.bn2[c0 + t], bsum[t]);
     }
 }
 
@@ -149,9 +203,16 @@ void split_ff(const double2* in, float4* out, size_t count, cudaStream_t st) {
     if (blocks > 0) k_split_ff<<<blocks, 256, 0, st>>>(in, out, count);
 }
 
-void launch_residual_ff(const ResidualFF& R, const ResJob* jobs, int nb, cudaStream_t st) {
+void launch_residual_ff(const ResidualFF& R, const ResJob* jobs, int nb, int m_max, cudaStream_t st) {
     k_split_solution<<<dim3(256, nb), 256, 0, st>>>(jobs, R.N, R.n, R.Cff, R.per);
-    k_residual_ff<<<dim3(R.N, nb), 256, 0, st>>>(R, jobs);
+    const int col_tiles = (std::max(m_max, 1) + CT - 1) / CT;
+    const int smem = (int)(sizeof(float4) * (RT * (KC + 1) + KC * CT));
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_residual_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = true;
+    }
+    k_residual_ff<<<dim3(((R.n + RT - 1) / RT) * col_tiles, R.N, nb), 256, smem, st>>>(R, jobs, col_tiles);
     launch_residual_finish(jobs, nb, st);
 }
 

@@ -139,7 +139,8 @@ __global__ void k_fill_int(int* p, int v, int cnt) {
 }
 
 // ---------------------------------------------------------------- orchestration
-int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, const SolveOut& o, cudaStream_t st) {
+int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, const SolveOut& o, cudaStream_t st,
+                const DensityAcc* dens) {
     const int n = c->n, N = s.N;
     const size_t nn = (size_t)n * n;
     // 1. contact data (FP64 cache, computed on a miss)
@@ -278,6 +279,11 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
         launch_observables(n, N, obs_d.as<ObsJob>(), nb, st);
         c->launches++;
         PWQT_CUDA(c, cudaGetLastError());
+        if (dens) {
+            DensityAcc d = *dens;
+            d.w = dens->w + e0;
+            PWQT_TRY(density_accumulate_batch(c, s, obs, E + e0, d, nb, st));
+        }
         // n_open (source, drain) per energy
         std::vector<int> nopen(2 * nb);
         for (int b = 0; b < nb; ++b) { nopen[2 * b] = ms[e0 + b]; nopen[2 * b + 1] = md[e0 + b]; }

@@ -44,5 +44,9 @@ struct ObsJob {
 
 void launch_sweep_fp64(const SweepSys& sys, const SweepJob* jobs, int nb, cudaStream_t st);
 void launch_observables(int n, int N, const ObsJob* jobs, int nb, cudaStream_t st);
+// rank-m updates of the density matrix from one batch of solved energies (density.cu);
+// E and the weights in d.w are this batch's
+int density_accumulate_batch(pwqt_ctx* c, System& s, const std::vector<ObsJob>& obs, const double* E, const DensityAcc& d, int nb,
+                             cudaStream_t st);
 
 }  // namespace pwqt

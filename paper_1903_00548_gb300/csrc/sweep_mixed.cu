@@ -274,24 +274,36 @@ __global__ void k_mx_load_r(MixSys S, int i, const int* __restrict__ active) {
     }
 }
 
-// w <- U^{-1} L^{-1} P w for node i: one CTA per energy; pivots composed into a
-// permutation, 32-row diagonal blocks solved in shared memory, off-diagonal updates
-// in parallel over (row, column).
+// w <- U^{-1} L^{-1} P w for node i.  The m right-hand sides are independent, so
+// every energy gets ceil(m / LC) CTAs of LC columns each; a CTA keeps its columns
+// in shared memory (n x LC), solves each 32-row diagonal block with one warp per
+// two columns (lane = row, the solved value broadcast by shuffle) and applies the
+// off-diagonal part of the factors to the rows below (forward) or above
+// (backward) in parallel over (row, column).
+constexpr int LC = 16;
+
+__device__ __forceinline__ float2 shfl2(float2 v, int src) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+size_t lusolve_smem(int n) { return ((n * sizeof(int) + 15) / 16) * 16 + sizeof(float2) * (PW * (PW + 1) + (size_t)n * LC); }
+
 __global__ void __launch_bounds__(NT) k_mx_lusolve(MixSys S, int i, const int* __restrict__ active) {
     const int e = blockIdx.x;
     if (!active[e]) return;
     const SweepJob& J = S.jobs[e];
     const int n = S.n, w = S.w, m = J.ms + J.md;
-    if (m == 0) return;
+    const int c0 = blockIdx.y * LC;
+    if (c0 >= m) return;
     extern __shared__ unsigned char sm[];
-    int* perm = reinterpret_cast<int*>(sm);                                  // n
-    float2* Ld = reinterpret_cast<float2*>(sm + ((n * sizeof(int) + 15) / 16) * 16);   // PW x (PW+1)
-    float2* strip = Ld + PW * (PW + 1);                                       // PW x m
+    int* perm = reinterpret_cast<int*>(sm);                                              // n
+    float2* Ld = reinterpret_cast<float2*>(sm + ((n * sizeof(int) + 15) / 16) * 16);     // PW x (PW+1)
+    float2* T = Ld + PW * (PW + 1);                                                      // n x LC
     const float2* F = S.F + e * S.sF + (size_t)i * n * n;
     const int* piv = S.piv + e * S.sP + (size_t)i * n;
     float2* W = S.XY + e * S.sXY + (size_t)i * n * w + n;     // row stride w
-    float2* T = S.Lb + e * S.sL;                               // n x m scratch, row stride m
-    if (threadIdx.x == 0) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) {
         for (int j = 0; j < n; ++j) perm[j] = j;
         for (int j = 0; j < n; ++j) {
             int p = piv[j];
@@ -299,78 +311,85 @@ __global__ void __launch_bounds__(NT) k_mx_lusolve(MixSys S, int i, const int* _
         }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < n * m; t += NT) {
-        int r = t / m, g = t % m;
-        T[(size_t)r * m + g] = W[(size_t)perm[r] * w + g];
+    for (int q = t; q < n * LC; q += NT) {
+        const int r = q / LC, g = q % LC;
+        T[q] = c0 + g < m ? W[(size_t)perm[r] * w + c0 + g] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    // forward, unit lower
+    // forward substitution, unit lower factor
     for (int kb = 0; kb < n; kb += PW) {
         const int wd = min(PW, n - kb);
-        for (int t = threadIdx.x; t < PW * PW; t += NT) {
-            int r = t / PW, c = t % PW;
+        for (int q = t; q < PW * PW; q += NT) {
+            const int r = q / PW, c = q % PW;
             Ld[r * (PW + 1) + c] = (r < wd && c < wd) ? F[(size_t)(kb + r) * n + kb + c] : make_float2(0.f, 0.f);
         }
-        for (int t = threadIdx.x; t < wd * m; t += NT) strip[t] = T[(size_t)(kb + t / m) * m + t % m];
         __syncthreads();
-        for (int g = threadIdx.x; g < m; g += NT)
-            for (int j = 1; j < wd; ++j) {
-                float2 a = strip[j * m + g];
-                for (int l = 0; l < j; ++l) {
-                    float2 L = Ld[j * (PW + 1) + l];
-                    ffma(a, make_float2(-L.x, -L.y), strip[l * m + g]);
+        for (int cc = 2 * warp; cc < 2 * warp + 2; ++cc) {
+            float2 v = lane < wd ? T[(kb + lane) * LC + cc] : make_float2(0.f, 0.f);
+            for (int j = 0; j + 1 < wd; ++j) {
+                const float2 aj = shfl2(v, j);
+                if (lane > j) {
+                    const float2 L = Ld[lane * (PW + 1) + j];
+                    ffma(v, make_float2(-L.x, -L.y), aj);
                 }
-                strip[j * m + g] = a;
             }
+            if (lane < wd) T[(kb + lane) * LC + cc] = v;
+        }
         __syncthreads();
-        for (int t = threadIdx.x; t < wd * m; t += NT) T[(size_t)(kb + t / m) * m + t % m] = strip[t];
-        for (int t = threadIdx.x; t < (n - kb - wd) * m; t += NT) {
-            int r = kb + wd + t / m, g = t % m;
-            float2 a = T[(size_t)r * m + g];
+        const int r0 = kb + wd;
+        for (int q = t; q < (n - r0) * LC; q += NT) {
+            const int r = r0 + q / LC, g = q % LC;
+            float2 a = T[r * LC + g];
             const float2* Fr = F + (size_t)r * n + kb;
             for (int l = 0; l < wd; ++l) {
-                float2 L = Fr[l];
-                ffma(a, make_float2(-L.x, -L.y), strip[l * m + g]);
+                const float2 L = Fr[l];
+                ffma(a, make_float2(-L.x, -L.y), T[(kb + l) * LC + g]);
             }
-            T[(size_t)r * m + g] = a;
+            T[r * LC + g] = a;
         }
         __syncthreads();
     }
-    // backward, upper with diagonal
+    // backward substitution, upper factor with its diagonal
     for (int kb = ((n - 1) / PW) * PW; kb >= 0; kb -= PW) {
         const int wd = min(PW, n - kb);
-        for (int t = threadIdx.x; t < PW * PW; t += NT) {
-            int r = t / PW, c = t % PW;
+        for (int q = t; q < PW * PW; q += NT) {
+            const int r = q / PW, c = q % PW;
             Ld[r * (PW + 1) + c] = (r < wd && c < wd) ? F[(size_t)(kb + r) * n + kb + c] : make_float2(r == c ? 1.f : 0.f, 0.f);
         }
-        for (int t = threadIdx.x; t < wd * m; t += NT) strip[t] = T[(size_t)(kb + t / m) * m + t % m];
         __syncthreads();
-        for (int g = threadIdx.x; g < m; g += NT)
+        for (int cc = 2 * warp; cc < 2 * warp + 2; ++cc) {
+            float2 v = lane < wd ? T[(kb + lane) * LC + cc] : make_float2(0.f, 0.f);
             for (int j = wd - 1; j >= 0; --j) {
-                float2 a = strip[j * m + g];
-                for (int l = j + 1; l < wd; ++l) {
-                    float2 U = Ld[j * (PW + 1) + l];
-                    ffma(a, make_float2(-U.x, -U.y), strip[l * m + g]);
+                if (lane == j) {
+                    float2 d = Ld[j * (PW + 1) + j];
+                    if (d.x == 0.f && d.y == 0.f) d = make_float2(1.f, 0.f);
+                    v = fdiv(v, d);
                 }
-                float2 d = Ld[j * (PW + 1) + j];
-                if (d.x == 0.f && d.y == 0.f) d = make_float2(1.f, 0.f);
-                strip[j * m + g] = fdiv(a, d);
+                const float2 aj = shfl2(v, j);
+                if (lane < j) {
+                    const float2 U = Ld[lane * (PW + 1) + j];
+                    ffma(v, make_float2(-U.x, -U.y), aj);
+                }
             }
+            if (lane < wd) T[(kb + lane) * LC + cc] = v;
+        }
         __syncthreads();
-        for (int t = threadIdx.x; t < wd * m; t += NT) T[(size_t)(kb + t / m) * m + t % m] = strip[t];
-        for (int t = threadIdx.x; t < kb * m; t += NT) {
-            int r = t / m, g = t % m;
-            float2 a = T[(size_t)r * m + g];
+        for (int q = t; q < kb * LC; q += NT) {
+            const int r = q / LC, g = q % LC;
+            float2 a = T[r * LC + g];
             const float2* Fr = F + (size_t)r * n + kb;
             for (int l = 0; l < wd; ++l) {
-                float2 U = Fr[l];
-                ffma(a, make_float2(-U.x, -U.y), strip[l * m + g]);
+                const float2 U = Fr[l];
+                ffma(a, make_float2(-U.x, -U.y), T[(kb + l) * LC + g]);
             }
-            T[(size_t)r * m + g] = a;
+            T[r * LC + g] = a;
         }
         __syncthreads();
     }
-    for (int t = threadIdx.x; t < n * m; t += NT) W[(size_t)(t / m) * w + t % m] = T[t];
+    for (int q = t; q < n * LC; q += NT) {
+        const int r = q / LC, g = q % LC;
+        if (c0 + g < m) W[(size_t)r * w + c0 + g] = T[q];
+    }
 }
 
 // c += d (FP64), active energies
@@ -509,18 +528,29 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         res[b].r_row_stride = m;
     }
     PWQT_CUDA(c, cudaMemcpyAsync(res_d, res.data(), sizeof(ResJob) * nb, cudaMemcpyHostToDevice, st));
-    const size_t lus_smem = ((n * sizeof(int) + 15) / 16) * 16 + sizeof(float2) * (PW * (PW + 1) + (size_t)PW * m);
+    const size_t lus_smem = lusolve_smem(n);
     if (lus_smem > 48 * 1024)
         PWQT_CUDA(c, cudaFuncSetAttribute(k_mx_lusolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lus_smem));
     std::vector<double> resid(nb, 1.0), prev(nb, 1e300);
     std::vector<int> iters(nb, 0), active(nb, 1), stall(nb, 0), bits(nb, 0);
     const double tol = c->opts.ir_tol;
     for (int it = 0;; ++it) {
+        if (c->profile) PWQT_CUDA(c, cudaEventRecord(c->ev0, st));
         PWQT_CUDA(c, cudaMemsetAsync(res[0].rn2, 0, sizeof(double) * 2 * (size_t)nb * m, st));
-        launch_residual_ff(RF, res_d, nb, st);
+        launch_residual_ff(RF, res_d, nb, m, st);
         c->launches += 3;
+        if (c->profile) PWQT_CUDA(c, cudaEventRecord(c->ev1, st));
         PWQT_CUDA(c, cudaMemcpyAsync(resid.data(), res[0].resid, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
         PWQT_CUDA(c, cudaStreamSynchronize(st));
+        if (c->profile) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+            c->prof_phase_ms[0] += ms;
+            if (it > 0) {
+                cudaEventElapsedTime(&ms, c->ev2, c->ev3);
+                c->prof_phase_ms[1] += ms;
+            }
+        }
         int any = 0;
         for (int b = 0; b < nb; ++b) {
             if (!active[b]) continue;
@@ -537,6 +567,10 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
             any = 1;
         }
         if (!any) break;
+        if (c->profile) {
+            PWQT_CUDA(c, cudaEventRecord(c->ev2, st));
+            c->prof_ir_iters++;
+        }
         PWQT_CUDA(c, cudaMemcpyAsync(active_d, active.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
         for (int i = 0; i < N; ++i) {
             float2* XYi = S.XY + (size_t)i * n * w;
@@ -548,7 +582,7 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
                 gemm(S.Lb, S.sL, n, XYp + n, S.sXY, w, XYp + n, S.sXY, w, XYi + n, S.sXY, w, XYi + n, S.sXY, w, m, n, m, n);
                 c->launches++;
             }
-            k_mx_lusolve<<<nb, NT, lus_smem, st>>>(S, i, active_d);
+            k_mx_lusolve<<<dim3(nb, (m + LC - 1) / LC), NT, lus_smem, st>>>(S, i, active_d);
             c->launches++;
         }
         for (int i = N - 2; i >= 0; --i) {
@@ -558,6 +592,7 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         }
         k_mx_update<<<dim3(256, nb), NT, 0, st>>>(S, active_d);
         c->launches++;
+        if (c->profile) PWQT_CUDA(c, cudaEventRecord(c->ev3, st));
         PWQT_CUDA(c, cudaGetLastError());
     }
     PWQT_CUDA(c, cudaMemcpyAsync(iters_dev, iters.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));

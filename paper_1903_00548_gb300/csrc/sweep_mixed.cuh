@@ -36,7 +36,7 @@ struct ResidualFF {
     float4* Cff; size_t per;                 // float-float copy of the solution, per-energy stride
 };
 void split_ff(const double2* in, float4* out, size_t count, cudaStream_t st);
-void launch_residual_ff(const ResidualFF& R, const ResJob* jobs, int nb, cudaStream_t st);
+void launch_residual_ff(const ResidualFF& R, const ResJob* jobs, int nb, int m_max, cudaStream_t st);
 void launch_residual_finish(const ResJob* jobs, int nb, cudaStream_t st);
 
 size_t mixed_bytes_per_energy(int n, int N, int m);

@@ -22,7 +22,9 @@ ST_SINGULAR_PIVOT, ST_MODE_COUNT, ST_IR_NO_CONVERGE, ST_DEGENERATE, ST_NEAR_UNIT
 
 EXPORTS = ["pwqt_create", "pwqt_destroy", "pwqt_last_error", "pwqt_assemble_intrinsic", "pwqt_set_enhancement",
            "pwqt_get_blocks", "pwqt_set_extrinsic", "pwqt_solve", "pwqt_solve_dev", "pwqt_prepare_leads",
-           "pwqt_cache_info", "pwqt_bands", "pwqt_kernel_launches", "pwqt_profile", "pwqt_solve_noalloc", "pwqt_cgemm_c64"]
+           "pwqt_cache_info", "pwqt_bands", "pwqt_kernel_launches", "pwqt_profile", "pwqt_solve_noalloc", "pwqt_cgemm_c64",
+           "pwqt_density_reset", "pwqt_accumulate_density", "pwqt_get_density_matrix", "pwqt_density_grid",
+           "pwqt_profile_refinement"]
 
 
 class PwqtError(RuntimeError):
@@ -74,6 +76,11 @@ def load(path: str = LIB_PATH):
     lib.pwqt_kernel_launches.argtypes = [P, C.POINTER(C.c_longlong), I]
     lib.pwqt_profile.argtypes = [P, I, dp, C.POINTER(C.c_longlong), dp, I]
     lib.pwqt_solve_noalloc.argtypes = [P, I, I, dp, P, P, P, P, P, P]
+    lib.pwqt_density_reset.argtypes = [P, I]
+    lib.pwqt_profile_refinement.argtypes = [P, dp, dp, C.POINTER(C.c_longlong)]
+    lib.pwqt_accumulate_density.argtypes = [P, I, I, dp, dp, D, D, D, I, ip]
+    lib.pwqt_get_density_matrix.argtypes = [P, I, dp, dp]
+    lib.pwqt_density_grid.argtypes = [P, I, I, I, dp]
     fp = C.POINTER(C.c_float)
     lib.pwqt_cgemm_c64.argtypes = [I, I, I, I, fp, I, fp, I, fp, I]
     for f in EXPORTS:
@@ -160,6 +167,7 @@ class Context:
         n = C.c_int()
         self._check(self.lib.pwqt_assemble_intrinsic(self.h, C.byref(cc), C.byref(f), gcut, n_bands, C.byref(n)))
         self.n = n.value
+        self.dim = cell.dim
         self.n_nodes = {}
         return self.n
 
@@ -176,6 +184,7 @@ class Context:
         self._check(self.lib.pwqt_set_enhancement(self.h, C.byref(cc), nb, _dptr(eps), _iptr(n_pw), _iptr(mx), _iptr(mz),
                                                   coef.ctypes.data_as(C.POINTER(C.c_double)), C.byref(n)))
         self.n = n.value
+        self.dim = cell.dim
         self.n_nodes = {}
         return self.n
 
@@ -224,6 +233,35 @@ class Context:
         self._check(self.lib.pwqt_solve_noalloc(self.h, sys, len(E), _dptr(E), g("T"), g("R"), g("T_ds"), g("node_n"),
                                                 g("status"), C.c_void_p(stream_ptr) if stream_ptr else None))
 
+    def density_reset(self, sys: int):
+        self._check(self.lib.pwqt_density_reset(self.h, sys))
+
+    def accumulate_density(self, sys: int, E, w, mu_s: float, mu_d: float, kT: float, precision: int = FP64):
+        """Solve at E and add w-weighted contributions to the density matrix; returns the statuses."""
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        w = np.ascontiguousarray(np.broadcast_to(w, E.shape), dtype=np.float64)
+        status = np.zeros(len(E), np.int32)
+        self._check(self.lib.pwqt_accumulate_density(self.h, sys, len(E), _dptr(E), _dptr(w), mu_s, mu_d, kT, precision,
+                                                     _iptr(status)))
+        return status
+
+    def density_matrix(self, sys: int):
+        """(rho_d (N, n, n), rho_u (N-1, n, n)) complex128."""
+        N, n = self.n_nodes[sys], self.n
+        rd = np.zeros((N, n, n), np.complex128)
+        ru = np.zeros((max(N - 1, 0), n, n), np.complex128)
+        ptr = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        self._check(self.lib.pwqt_get_density_matrix(self.h, sys, ptr(rd), ptr(ru)))
+        return rd, ru
+
+    def density_grid(self, sys: int, nx: int, nz: int):
+        """n(r) per element: array (N-1, nx or 1, nz)."""
+        N = self.n_nodes[sys]
+        nxe = nx if getattr(self, "dim", 1) == 2 else 1
+        out = np.zeros((max(N - 1, 0), nxe, nz))
+        self._check(self.lib.pwqt_density_grid(self.h, sys, nx, nz, _dptr(out)))
+        return out
+
     def cache_info(self):
         e, b = C.c_int(), C.c_size_t()
         self._check(self.lib.pwqt_cache_info(self.h, C.byref(e), C.byref(b)))
@@ -240,6 +278,12 @@ class Context:
         self._check(self.lib.pwqt_profile(self.h, 1 if enable else 0, C.byref(ms), C.byref(cnt), C.byref(fl),
                                           1 if reset else 0))
         return ms.value, cnt.value, fl.value
+
+    def profile_refinement(self):
+        """(residual ms, correction ms, refinement iterations) recorded while profiling."""
+        r, c, it = C.c_double(), C.c_double(), C.c_longlong()
+        self._check(self.lib.pwqt_profile_refinement(self.h, C.byref(r), C.byref(c), C.byref(it)))
+        return r.value, c.value, it.value
 
     def kernel_launches(self, reset: bool = False) -> int:
         v = C.c_longlong()
