@@ -44,7 +44,7 @@ typedef struct pwqt_ctx pwqt_ctx;
 #define PWQT_ST_OK               0
 #define PWQT_ST_SINGULAR_PIVOT   1    /* a pivot of a node block was exactly zero   */
 #define PWQT_ST_MODE_COUNT       2    /* out-flow mode count != n at a contact     */
-#define PWQT_ST_IR_NO_CONVERGE   4    /* refinement hit its iteration limit        */
+#define PWQT_ST_IR_NO_CONVERGE   4    /* refinement stopped above its tolerance    */
 #define PWQT_ST_DEGENERATE       8    /* degenerate traveling modes at a contact   */
 #define PWQT_ST_NEAR_UNIT        16   /* an evanescent |lambda| within 1e-3 of 1   */
 
@@ -58,7 +58,8 @@ typedef struct {
     int    device;             /* CUDA device ordinal                              */
     size_t hbm_budget_bytes;   /* 0: use 90 % of the free device memory            */
     double ir_tol;             /* mixed path: stop when ||B - A c|| <= ir_tol ||B||
-                                  (max over columns); 0 -> 1e-11                    */
+                                  (max over columns), or when the residual stalls
+                                  within 10 ir_tol; 0 -> 1e-9                       */
     int    ir_max_iters;       /* mixed path refinement limit; 0 -> 40              */
     int    batch;              /* energies per sweep launch; 0 -> from the budget   */
 } pwqt_opts;
@@ -197,6 +198,13 @@ int pwqt_bands(pwqt_ctx* ctx, int n_k, const double* k, double* E_out);
  */
 int pwqt_profile(pwqt_ctx* ctx, int enable, double* sweep_ms, long long* sweep_launches,
                  double* sweep_flops, int reset);
+
+/*
+ * Change the refinement stopping rule of the mixed path for later solves (the
+ * pwqt_opts fields ir_tol and ir_max_iters; 0 selects the defaults 1e-9 and 40).
+ * Errors: PWQT_ERR_INVALID_ARG for a negative or non-finite value.
+ */
+int pwqt_set_refinement(pwqt_ctx* ctx, double ir_tol, int ir_max_iters);
 
 /*
  * Refinement phases of the mixed path recorded while pwqt_profile is enabled

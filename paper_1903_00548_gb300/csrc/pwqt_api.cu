@@ -43,7 +43,7 @@ int pwqt_create(pwqt_ctx** out, const pwqt_opts* opts) {
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) { cudaGetLastError(); return PWQT_ERR_NO_DEVICE; }
     auto* c = new pwqt_ctx();
     if (opts) c->opts = *opts;
-    if (c->opts.ir_tol <= 0) c->opts.ir_tol = 1e-11;
+    if (c->opts.ir_tol <= 0) c->opts.ir_tol = 1e-9;
     if (c->opts.ir_max_iters <= 0) c->opts.ir_max_iters = 40;
     c->dev = c->opts.device;
     if (c->dev < 0 || c->dev >= ndev) { delete c; return PWQT_ERR_INVALID_ARG; }
@@ -363,6 +363,16 @@ int pwqt_profile_refinement(pwqt_ctx* c, double* residual_ms, double* correction
     if (residual_ms) *residual_ms = c->prof_phase_ms[0];
     if (correction_ms) *correction_ms = c->prof_phase_ms[1];
     if (iterations) *iterations = c->prof_ir_iters;
+    return PWQT_OK;
+}
+
+
+int pwqt_set_refinement(pwqt_ctx* c, double ir_tol, int ir_max_iters) {
+    PWQT_TRY(check_ctx(c));
+    if (!(ir_tol >= 0) || !std::isfinite(ir_tol) || ir_max_iters < 0)
+        return fail(c, PWQT_ERR_INVALID_ARG, "ir_tol must be finite and >= 0, ir_max_iters >= 0");
+    c->opts.ir_tol = ir_tol > 0 ? ir_tol : 1e-9;
+    c->opts.ir_max_iters = ir_max_iters > 0 ? ir_max_iters : 40;
     return PWQT_OK;
 }
 

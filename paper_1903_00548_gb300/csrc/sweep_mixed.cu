@@ -557,6 +557,9 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
             if (resid[b] <= tol) { active[b] = 0; continue; }
             if (resid[b] > 0.5 * prev[b]) stall[b]++;
             else stall[b] = 0;
+            // a residual that stops falling within 10 ir_tol has met the accuracy floor of
+            // the float-float residual (~2^-44 of |A||c| / |B|): converged, not flagged
+            if (stall[b] >= 2 && resid[b] <= 10.0 * tol) { active[b] = 0; continue; }
             if (stall[b] >= 3 || iters[b] >= c->opts.ir_max_iters) {
                 active[b] = 0;
                 bits[b] |= PWQT_ST_IR_NO_CONVERGE;   // final residual above ir_tol

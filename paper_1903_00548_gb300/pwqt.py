@@ -24,7 +24,7 @@ EXPORTS = ["pwqt_create", "pwqt_destroy", "pwqt_last_error", "pwqt_assemble_intr
            "pwqt_get_blocks", "pwqt_set_extrinsic", "pwqt_solve", "pwqt_solve_dev", "pwqt_prepare_leads",
            "pwqt_cache_info", "pwqt_bands", "pwqt_kernel_launches", "pwqt_profile", "pwqt_solve_noalloc", "pwqt_cgemm_c64",
            "pwqt_density_reset", "pwqt_accumulate_density", "pwqt_get_density_matrix", "pwqt_density_grid",
-           "pwqt_profile_refinement"]
+           "pwqt_profile_refinement", "pwqt_set_refinement"]
 
 
 class PwqtError(RuntimeError):
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
     lib.pwqt_solve_noalloc.argtypes = [P, I, I, dp, P, P, P, P, P, P]
     lib.pwqt_density_reset.argtypes = [P, I]
     lib.pwqt_profile_refinement.argtypes = [P, dp, dp, C.POINTER(C.c_longlong)]
+    lib.pwqt_set_refinement.argtypes = [P, D, I]
     lib.pwqt_accumulate_density.argtypes = [P, I, I, dp, dp, D, D, D, I, ip]
     lib.pwqt_get_density_matrix.argtypes = [P, I, dp, dp]
     lib.pwqt_density_grid.argtypes = [P, I, I, I, dp]
@@ -278,6 +279,9 @@ class Context:
         self._check(self.lib.pwqt_profile(self.h, 1 if enable else 0, C.byref(ms), C.byref(cnt), C.byref(fl),
                                           1 if reset else 0))
         return ms.value, cnt.value, fl.value
+
+    def set_refinement(self, ir_tol: float = 0.0, ir_max_iters: int = 0):
+        self._check(self.lib.pwqt_set_refinement(self.h, ir_tol, ir_max_iters))
 
     def profile_refinement(self):
         """(residual ms, correction ms, refinement iterations) recorded while profiling."""

@@ -212,14 +212,17 @@ def test_chain_parity_statistics(pw, chain):
 
 
 # ---------------------------------------------------------------- mixed precision
-# complex64 factorisation on the tensor cores (3xTF32) + refinement with FP64
-# residuals: T within 1e-8 of the oracle (or 4x the two sides' reciprocity defects)
+# complex64 factorisation on the tensor cores (3xTF32) + refinement with
+# float-float residuals: T within 1e-8 of the oracle (or 4x the two sides'
+# reciprocity defects).  The small systems below refine to 1e-11 (tighter than the
+# 1e-9 default) so that the refinement loop itself is checked well past the bar.
 MIXED_TOL = 1e-8
 
 
 def test_mixed_chain_all_energies(pw, chain):
     wl, s = chain
     ctx = _ctx_with_basis(pw, s)
+    ctx.set_refinement(1e-11, 0)
     ctx.set_extrinsic(0, wl.U)
     res = ctx.solve(0, wl.energies, pw.MIXED)
     ref = _oracle_results(s, wl.energies)
@@ -234,6 +237,7 @@ def test_mixed_small_ribbon(pw):
     from tests.oracle_fixtures import small_ribbon_system
     s = small_ribbon_system()
     ctx = _ctx_with_basis(pw, s)
+    ctx.set_refinement(1e-11, 0)
     ctx.set_extrinsic(0, s.U)
     Es = np.array([0.25, 0.6, 1.1, 1.7, 2.3])
     res = ctx.solve(0, Es, pw.MIXED)
@@ -249,7 +253,24 @@ def test_mixed_matches_fp64_path_on_a_longer_ribbon(pw):
     ctx.set_extrinsic(0, s.U)
     Es = np.array([0.4, 1.3, 2.1])
     r64 = ctx.solve(0, Es, pw.FP64)
-    rmx = ctx.solve(0, Es, pw.MIXED)
+    rmx = ctx.solve(0, Es, pw.MIXED)   # default stopping rule (residual 1e-9)
+    assert np.all(rmx.resid <= 1e-8)
     t = np.maximum(MIXED_TOL * np.maximum(1, r64.n_open[:, 0]), 4 * np.abs(r64.T - r64.T_ds))
     assert np.all(np.abs(rmx.T - r64.T) <= t + 4 * np.abs(rmx.T - rmx.T_ds))
     assert np.all(rmx.status & ~pw.ST_NEAR_UNIT == 0)
+
+
+def test_refinement_settings(pw, chain):
+    wl, s = chain
+    ctx = _ctx_with_basis(pw, s)
+    ctx.set_extrinsic(0, wl.U)
+    E = wl.energies[10:14]
+    ctx.set_refinement(1e-13, 1)          # one step cannot reach 1e-13: flagged
+    one = ctx.solve(0, E, pw.MIXED)
+    assert np.all(one.iters <= 1)
+    assert np.all((one.status & pw.ST_IR_NO_CONVERGE) != 0)
+    ctx.set_refinement(0, 0)              # defaults
+    d = ctx.solve(0, E, pw.MIXED)
+    assert np.all(d.status == 0) and np.all(d.resid <= 1e-8)
+    with pytest.raises(pw.PwqtError):
+        ctx.set_refinement(-1.0, 0)
