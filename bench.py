@@ -37,6 +37,10 @@ UNIT = "energy-solves/s"
 L2_BYTES = 129 * 2 ** 20
 # nominal dense rates of GB300 used to scale the measured bf16 peak to other dtypes
 NOMINAL_TFLOPS = {"bf16": 2250.0, "tf32": 1100.0, "f64": 1.25}
+# FP32 instructions per complex multiply-add of the float-float residual: four
+# float-float multiply-adds of 11 instructions (product, its FMA error, two cross
+# terms, two-sum of the leading parts, low-part update)
+FF_INST_PER_CMAC = 44
 
 
 def peaks():
@@ -283,7 +287,7 @@ def run_ours(args, world, rank, local):
     ev_e.record(stream)
     torch.cuda.synchronize(dev)
     barrier(world)
-    clk = clocks.stop()
+    clk_info = clocks.stop()
     total_ms = ev_s.elapsed_time(ev_e)
     per_step = [a.elapsed_time(b) for a, b in step_ms]
     launches = (ctx.kernel_launches() - launches0) // max(1, args.steps)
@@ -329,17 +333,37 @@ def run_ours(args, world, rank, local):
                 "solve_plus_accumulate_s": t_acc, "grid_s": t_grid, "grid": [nx, nz],
                 "grid_points": int(grid.size), "n_max": float(grid.max())}
 
-    # roofline of the dominant kernel (the block sweep)
+    # roofline of the block sweep (tensor cores on the mixed path, FP64 pipe otherwise)
     bf16, hbm, src = peaks()
     dtype = "f64" if prec == pw.FP64 else "tf32"
     peak = bf16 * NOMINAL_TFLOPS[dtype] / NOMINAL_TFLOPS["bf16"]
     achieved = (sweep_flops / max(sweep_n, 1)) / (sweep_ms / max(sweep_n, 1) / 1e3) / 1e12 if sweep_n else None
-    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
-            "kernel": "k_sweep_fp64" if prec == pw.FP64 else "mixed block sweep",
-            "peak_source": f"{src} bf16 x nominal {dtype}/bf16 ratio",
-            "flops_per_launch": sweep_flops / max(sweep_n, 1), "avg_launch_ms": sweep_ms / max(sweep_n, 1),
-            "launches": sweep_n}
+    roof_sweep = {"bound": "tensor" if prec == pw.MIXED else "fp64", "achieved": achieved, "peak": peak,
+                  "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                  "kernel": "k_sweep_fp64" if prec == pw.FP64 else "block sweep (k_cgemm_tc + k_mx_panel + k_mx_trsm_up)",
+                  "peak_source": f"{src} bf16 x nominal {dtype}/bf16 ratio",
+                  "flops_per_launch": sweep_flops / max(sweep_n, 1), "avg_launch_ms": sweep_ms / max(sweep_n, 1),
+                  "launches": sweep_n}
+    roof = roof_sweep
+    if prec == pw.MIXED and ir_res_ms > 0:
+        # the dominant kernel of the mixed path: the float-float residual on the FP32 pipes.
+        # Algorithmic work per evaluation and energy: (3N - 2) n^2 m complex MACs (the
+        # block-tridiagonal rows), FF_INST_PER_CMAC FP32 instructions each; evaluations per
+        # energy = refinement iterations + 1.  Peak: one FP32 instruction per lane per clock.
+        m_e = nopen.sum(1).astype(np.float64)
+        evals = iters.astype(np.float64) + 1.0
+        inst = float(np.sum(evals * m_e)) * (3 * N - 2) * float(n) * n * FF_INST_PER_CMAC
+        launches_res = float(np.max(evals))
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        clk = (clk_info.get("sm_max_mhz") or 2070.0) * 1e6
+        peak_alu = sms * 128 * clk / 1e12
+        res_ms_step = ir_res_ms / args.steps
+        ach = inst / (res_ms_step / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak_alu, "unit": "T FP32 instructions/s",
+                "frac": ach / peak_alu, "traffic": None, "kernel": "k_residual_ff",
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x {clk / 1e6:.0f} MHz (max SM clock)",
+                "inst_per_launch": inst / launches_res, "avg_launch_ms": res_ms_step / launches_res,
+                "launches": launches_res * args.steps, "inst_per_complex_mac": FF_INST_PER_CMAC}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -352,7 +376,8 @@ def run_ours(args, world, rank, local):
             "latency_ms": {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99)),
                            "unit": f"per step of {batch} energies"},
             "sigma_cold_s_per_energy": t_leads / max(1, len(set(E.tolist()))), "setup_s": t_setup,
-            "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "density": dens,
+            "gpu_launches": int(launches), "clocks": clk_info, "roofline": roof, "roofline_sweep": roof_sweep,
+            "density": dens,
             "phases_ms_per_step": {"sweep": sweep_ms / args.steps, "refine_residual": ir_res_ms / args.steps,
                                    "refine_correction": ir_cor_ms / args.steps,
                                    "refine_iterations": ir_iters / args.steps,

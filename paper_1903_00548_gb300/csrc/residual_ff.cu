@@ -77,7 +77,9 @@ __global__ void k_split_ff(const double2* __restrict__ in, float4* __restrict__ 
 }
 
 // solution c (FP64, node stride / row stride of the job) -> float-float copy with the same layout
-__global__ void k_split_solution(const ResJob* __restrict__ jobs, int N, int n, float4* __restrict__ out, size_t per) {
+__global__ void k_split_solution(const ResJob* __restrict__ jobs, int N, int n, float4* __restrict__ out, size_t per,
+                                 const int* __restrict__ active) {
+    if (active && !active[blockIdx.y]) return;
     const ResJob J = jobs[blockIdx.y];
     const int m = J.ms + J.md;
     const size_t tot = (size_t)N * J.node_stride;
@@ -98,7 +100,9 @@ constexpr int RT = 64;    // rows per CTA
 constexpr int CT = 32;    // columns per CTA
 constexpr int KC = 32;    // K chunk
 
-__global__ void __launch_bounds__(256) k_residual_ff(ResidualFF R, const ResJob* __restrict__ jobs, int col_tiles) {
+__global__ void __launch_bounds__(256) k_residual_ff(ResidualFF R, const ResJob* __restrict__ jobs, int col_tiles,
+                                                     const int* __restrict__ active) {
+    if (active && !active[blockIdx.z]) return;
     extern __shared__ float4 rsm[];
     float4 (*As)[KC + 1] = reinterpret_cast<float4 (*)[KC + 1]>(rsm);          // [RT][KC + 1]
     float4 (*Cs)[CT] = reinterpret_cast<float4 (*)[CT]>(rsm + RT * (KC + 1));   // [KC][CT]
@@ -203,8 +207,8 @@ void split_ff(const double2* in, float4* out, size_t count, cudaStream_t st) {
     if (blocks > 0) k_split_ff<<<blocks, 256, 0, st>>>(in, out, count);
 }
 
-void launch_residual_ff(const ResidualFF& R, const ResJob* jobs, int nb, int m_max, cudaStream_t st) {
-    k_split_solution<<<dim3(256, nb), 256, 0, st>>>(jobs, R.N, R.n, R.Cff, R.per);
+void launch_residual_ff(const ResidualFF& R, const ResJob* jobs, int nb, int m_max, const int* active, cudaStream_t st) {
+    k_split_solution<<<dim3(256, nb), 256, 0, st>>>(jobs, R.N, R.n, R.Cff, R.per, active);
     const int col_tiles = (std::max(m_max, 1) + CT - 1) / CT;
     const int smem = (int)(sizeof(float4) * (RT * (KC + 1) + KC * CT));
     static bool attr = false;
@@ -212,8 +216,8 @@ void launch_residual_ff(const ResidualFF& R, const ResJob* jobs, int nb, int m_m
         cudaFuncSetAttribute(k_residual_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
-    k_residual_ff<<<dim3(((R.n + RT - 1) / RT) * col_tiles, R.N, nb), 256, smem, st>>>(R, jobs, col_tiles);
-    launch_residual_finish(jobs, nb, st);
+    k_residual_ff<<<dim3(((R.n + RT - 1) / RT) * col_tiles, R.N, nb), 256, smem, st>>>(R, jobs, col_tiles, active);
+    launch_residual_finish(jobs, nb, st, active);
 }
 
 }  // namespace pwqt

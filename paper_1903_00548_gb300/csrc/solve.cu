@@ -109,9 +109,9 @@ __global__ void k_residual_fp64(SweepSys sys, const ResJob* __restrict__ jobs) {
     }
 }
 
-__global__ void k_residual_finish(const ResJob* __restrict__ jobs, int nb) {
+__global__ void k_residual_finish(const ResJob* __restrict__ jobs, int nb, const int* __restrict__ active) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
+    if (b >= nb || (active && !active[b])) return;
     const ResJob J = jobs[b];
     int m = J.ms + J.md;
     double worst = 0.0;
@@ -123,8 +123,8 @@ __global__ void k_residual_finish(const ResJob* __restrict__ jobs, int nb) {
     *J.resid = worst;
 }
 
-void launch_residual_finish(const ResJob* jobs, int nb, cudaStream_t st) {
-    k_residual_finish<<<(nb + 127) / 128, 128, 0, st>>>(jobs, nb);
+void launch_residual_finish(const ResJob* jobs, int nb, cudaStream_t st, const int* active) {
+    k_residual_finish<<<(nb + 127) / 128, 128, 0, st>>>(jobs, nb, active);
 }
 
 void launch_residual_fp64(const SweepSys& sys, const ResJob* jobs, int nb, cudaStream_t st) {

@@ -116,14 +116,16 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
         P[t] = c < wd ? F[(size_t)(k0 + r) * n + k0 + c] : make_float2(0.f, 0.f);
     }
     __syncthreads();
+    // pivot candidates of column 0; afterwards each elimination pass also finds the
+    // candidates of the next column while it updates the rows
+    float best = -1.f;
+    int idx = 0;
+    for (int r = threadIdx.x; r < rows; r += NT) {
+        const float2 v = P[r * PW];
+        const float a = fabsf(v.x) + fabsf(v.y);
+        if (a > best) { best = a; idx = r; }
+    }
     for (int j = 0; j < wd; ++j) {
-        float best = -1.f;
-        int idx = j;
-        for (int r = j + threadIdx.x; r < rows; r += NT) {
-            float2 v = P[r * PW + j];
-            float a = fabsf(v.x) + fabsf(v.y);
-            if (a > best) { best = a; idx = r; }
-        }
         for (int o = 16; o > 0; o >>= 1) {
             float ov = __shfl_down_sync(0xffffffff, best, o);
             int oi = __shfl_down_sync(0xffffffff, idx, o);
@@ -134,8 +136,9 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
         if (threadIdx.x == 0) {
             for (int q = 1; q < NT / 32; ++q)
                 if (bv[q] > bv[0] || (bv[q] == bv[0] && bi[q] < bi[0])) { bv[0] = bv[q]; bi[0] = bi[q]; }
-            prow[j] = bi[0];
-            piv[k0 + j] = k0 + bi[0];
+            const int pr = bv[0] < 0.f ? j : bi[0];   // no candidate rows: keep the diagonal
+            prow[j] = pr;
+            piv[k0 + j] = k0 + pr;
         }
         __syncthreads();
         const int p = prow[j];
@@ -147,13 +150,19 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
         __syncthreads();
         float2 pv = P[j * PW + j];
         if (pv.x == 0.f && pv.y == 0.f) { st |= PWQT_ST_SINGULAR_PIVOT; pv = make_float2(1.f, 0.f); }
-        for (int r = j + 1 + threadIdx.x; r < rows; r += NT) P[r * PW + j] = fdiv(P[r * PW + j], pv);
-        __syncthreads();
-        const int cols = wd - j - 1;
-        for (int t = threadIdx.x; t < (rows - j - 1) * cols; t += NT) {
-            int r = j + 1 + t / cols, c = j + 1 + t % cols;
-            float2 l = P[r * PW + j];
-            ffma(P[r * PW + c], make_float2(-l.x, -l.y), P[j * PW + c]);
+        const float2 inv = fdiv(make_float2(1.f, 0.f), pv);
+        best = -1.f;
+        idx = j + 1;
+        for (int r = j + 1 + threadIdx.x; r < rows; r += NT) {
+            const float2 x = P[r * PW + j];
+            const float2 l = make_float2(x.x * inv.x - x.y * inv.y, x.x * inv.y + x.y * inv.x);
+            P[r * PW + j] = l;
+            for (int c = j + 1; c < wd; ++c) ffma(P[r * PW + c], make_float2(-l.x, -l.y), P[j * PW + c]);
+            if (j + 1 < wd) {
+                const float2 v = P[r * PW + j + 1];
+                const float a = fabsf(v.x) + fabsf(v.y);
+                if (a > best) { best = a; idx = r; }
+            }
         }
         __syncthreads();
     }
@@ -161,22 +170,23 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
         int r = t / wd, c = t % wd;
         F[(size_t)(k0 + r) * n + k0 + c] = P[r * PW + c];
     }
-    // row interchanges on the other columns of F_i and on XY_i, in order
+    // row interchanges on the other columns of F_i and on XY_i, in order; every
+    // thread owns whole columns, so the swaps need no barrier between them
     const int ncolF = n - wd;
-    for (int j = 0; j < wd; ++j) {
-        const int p = prow[j];
-        if (p == j) continue;
-        const int ra = k0 + j, rb = k0 + p;
-        for (int c = threadIdx.x; c < ncolF + w; c += NT) {
-            if (c < ncolF) {
-                int col = c < k0 ? c : c + wd;
-                float2 a = F[(size_t)ra * n + col]; F[(size_t)ra * n + col] = F[(size_t)rb * n + col]; F[(size_t)rb * n + col] = a;
-            } else {
-                int col = c - ncolF;
-                float2 a = XY[(size_t)ra * w + col]; XY[(size_t)ra * w + col] = XY[(size_t)rb * w + col]; XY[(size_t)rb * w + col] = a;
-            }
+    for (int c = threadIdx.x; c < ncolF + w; c += NT) {
+        float2* base;
+        size_t ld;
+        if (c < ncolF) { base = F + (c < k0 ? c : c + wd); ld = n; }
+        else { base = XY + (c - ncolF); ld = w; }
+        for (int j = 0; j < wd; ++j) {
+            const int p = prow[j];
+            if (p == j) continue;
+            float2* a = base + (size_t)(k0 + j) * ld;
+            float2* b = base + (size_t)(k0 + p) * ld;
+            const float2 x = *a;
+            *a = *b;
+            *b = x;
         }
-        __syncthreads();
     }
     __syncthreads();
     // strip: rows k0..k0+wd of [F cols k0+wd..n | XY] <- L11^{-1} strip (unit lower)
@@ -286,7 +296,36 @@ __device__ __forceinline__ float2 shfl2(float2 v, int src) {
     return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
-size_t lusolve_smem(int n) { return ((n * sizeof(int) + 15) / 16) * 16 + sizeof(float2) * (PW * (PW + 1) + (size_t)n * LC); }
+constexpr int LR = 64;   // factor rows staged per chunk of the off-diagonal updates
+
+size_t lusolve_smem(int n) {
+    return ((n * sizeof(int) + 15) / 16) * 16 + sizeof(float2) * (PW * (PW + 1) + (size_t)LR * (PW + 1) + (size_t)n * LC);
+}
+
+// T[r][:] -= F[r][kb .. kb+wd) T[kb .. kb+wd)[:] for rows r in [r_begin, r_end), staged LR rows at a time
+__device__ __forceinline__ void lu_offdiag(const float2* __restrict__ F, int n, int kb, int wd, int r_begin, int r_end,
+                                           float2* Fs, float2* T) {
+    const int t = threadIdx.x;
+    for (int rc = r_begin; rc < r_end; rc += LR) {
+        const int rows = min(LR, r_end - rc);
+        for (int q = t; q < LR * PW; q += NT) {
+            const int rr = q / PW, l = q % PW;
+            Fs[rr * (PW + 1) + l] = (rr < rows && l < wd) ? F[(size_t)(rc + rr) * n + kb + l] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        for (int q = t; q < rows * LC; q += NT) {
+            const int rr = q / LC, g = q % LC;
+            float2 a = T[(rc + rr) * LC + g];
+#pragma unroll 8
+            for (int l = 0; l < wd; ++l) {   // rows kb + l < n of T only
+                const float2 L = Fs[rr * (PW + 1) + l];
+                ffma(a, make_float2(-L.x, -L.y), T[(kb + l) * LC + g]);
+            }
+            T[(rc + rr) * LC + g] = a;
+        }
+        __syncthreads();
+    }
+}
 
 __global__ void __launch_bounds__(NT) k_mx_lusolve(MixSys S, int i, const int* __restrict__ active) {
     const int e = blockIdx.x;
@@ -298,7 +337,8 @@ __global__ void __launch_bounds__(NT) k_mx_lusolve(MixSys S, int i, const int* _
     extern __shared__ unsigned char sm[];
     int* perm = reinterpret_cast<int*>(sm);                                              // n
     float2* Ld = reinterpret_cast<float2*>(sm + ((n * sizeof(int) + 15) / 16) * 16);     // PW x (PW+1)
-    float2* T = Ld + PW * (PW + 1);                                                      // n x LC
+    float2* Fs = Ld + PW * (PW + 1);                                                     // LR x (PW+1)
+    float2* T = Fs + LR * (PW + 1);                                                      // n x LC
     const float2* F = S.F + e * S.sF + (size_t)i * n * n;
     const int* piv = S.piv + e * S.sP + (size_t)i * n;
     float2* W = S.XY + e * S.sXY + (size_t)i * n * w + n;     // row stride w
@@ -336,18 +376,7 @@ __global__ void __launch_bounds__(NT) k_mx_lusolve(MixSys S, int i, const int* _
             if (lane < wd) T[(kb + lane) * LC + cc] = v;
         }
         __syncthreads();
-        const int r0 = kb + wd;
-        for (int q = t; q < (n - r0) * LC; q += NT) {
-            const int r = r0 + q / LC, g = q % LC;
-            float2 a = T[r * LC + g];
-            const float2* Fr = F + (size_t)r * n + kb;
-            for (int l = 0; l < wd; ++l) {
-                const float2 L = Fr[l];
-                ffma(a, make_float2(-L.x, -L.y), T[(kb + l) * LC + g]);
-            }
-            T[r * LC + g] = a;
-        }
-        __syncthreads();
+        lu_offdiag(F, n, kb, wd, kb + wd, n, Fs, T);
     }
     // backward substitution, upper factor with its diagonal
     for (int kb = ((n - 1) / PW) * PW; kb >= 0; kb -= PW) {
@@ -374,17 +403,7 @@ __global__ void __launch_bounds__(NT) k_mx_lusolve(MixSys S, int i, const int* _
             if (lane < wd) T[(kb + lane) * LC + cc] = v;
         }
         __syncthreads();
-        for (int q = t; q < kb * LC; q += NT) {
-            const int r = q / LC, g = q % LC;
-            float2 a = T[r * LC + g];
-            const float2* Fr = F + (size_t)r * n + kb;
-            for (int l = 0; l < wd; ++l) {
-                const float2 U = Fr[l];
-                ffma(a, make_float2(-U.x, -U.y), T[(kb + l) * LC + g]);
-            }
-            T[r * LC + g] = a;
-        }
-        __syncthreads();
+        lu_offdiag(F, n, kb, wd, 0, kb, Fs, T);
     }
     for (int q = t; q < n * LC; q += NT) {
         const int r = q / LC, g = q % LC;
@@ -534,10 +553,11 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
     std::vector<double> resid(nb, 1.0), prev(nb, 1e300);
     std::vector<int> iters(nb, 0), active(nb, 1), stall(nb, 0), bits(nb, 0);
     const double tol = c->opts.ir_tol;
+    PWQT_CUDA(c, cudaMemcpyAsync(active_d, active.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
     for (int it = 0;; ++it) {
         if (c->profile) PWQT_CUDA(c, cudaEventRecord(c->ev0, st));
         PWQT_CUDA(c, cudaMemsetAsync(res[0].rn2, 0, sizeof(double) * 2 * (size_t)nb * m, st));
-        launch_residual_ff(RF, res_d, nb, m, st);
+        launch_residual_ff(RF, res_d, nb, m, active_d, st);   // energies still refining
         c->launches += 3;
         if (c->profile) PWQT_CUDA(c, cudaEventRecord(c->ev1, st));
         PWQT_CUDA(c, cudaMemcpyAsync(resid.data(), res[0].resid, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));

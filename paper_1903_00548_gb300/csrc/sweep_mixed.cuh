@@ -36,8 +36,9 @@ struct ResidualFF {
     float4* Cff; size_t per;                 // float-float copy of the solution, per-energy stride
 };
 void split_ff(const double2* in, float4* out, size_t count, cudaStream_t st);
-void launch_residual_ff(const ResidualFF& R, const ResJob* jobs, int nb, int m_max, cudaStream_t st);
-void launch_residual_finish(const ResJob* jobs, int nb, cudaStream_t st);
+// energies with active[b] == 0 (may be NULL: all) are skipped and keep their last residual
+void launch_residual_ff(const ResidualFF& R, const ResJob* jobs, int nb, int m_max, const int* active, cudaStream_t st);
+void launch_residual_finish(const ResJob* jobs, int nb, cudaStream_t st, const int* active = nullptr);
 
 size_t mixed_bytes_per_energy(int n, int N, int m);
 int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJob>& jobs, SweepJob* jobs_d,
