@@ -41,6 +41,12 @@ NOMINAL_TFLOPS = {"bf16": 2250.0, "tf32": 1100.0, "f64": 1.25}
 # float-float multiply-adds of 11 instructions (product, its FMA error, two cross
 # terms, two-sum of the leading parts, low-part update)
 FF_INST_PER_CMAC = 44
+# DRAM bytes (read + write) of one k_residual_ff launch per (node, energy) at block 512 and
+# ~91 injected modes, from the ncu capture summarised in
+# profiles/k_residual_ff_ribbon512_n20_b8.md (1.807 GB for 20 nodes x 8 energies); the
+# kernel re-reads its blocks once per node, energy and column tile, so a full launch
+# scales with nodes x energies.  None once the kernel changes.
+RESID_DRAM_BYTES_PER_NODE_ENERGY = 1.807e9 / 160
 
 
 def peaks():
@@ -359,8 +365,12 @@ def run_ours(args, world, rank, local):
         peak_alu = sms * 128 * clk / 1e12
         res_ms_step = ir_res_ms / args.steps
         ach = inst / (res_ms_step / 1e3) / 1e12
+        traffic = None
+        if RESID_DRAM_BYTES_PER_NODE_ENERGY is not None and n == 512:
+            traffic = RESID_DRAM_BYTES_PER_NODE_ENERGY * N * float(np.sum(evals)) / launches_res
         roof = {"bound": "alu", "achieved": ach, "peak": peak_alu, "unit": "T FP32 instructions/s",
-                "frac": ach / peak_alu, "traffic": None, "kernel": "k_residual_ff",
+                "frac": ach / peak_alu, "traffic": traffic, "traffic_unit": "bytes per launch (ncu, scaled)",
+                "kernel": "k_residual_ff",
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x {clk / 1e6:.0f} MHz (max SM clock)",
                 "inst_per_launch": inst / launches_res, "avg_launch_ms": res_ms_step / launches_res,
                 "launches": launches_res * args.steps, "inst_per_complex_mac": FF_INST_PER_CMAC}

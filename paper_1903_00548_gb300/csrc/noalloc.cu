@@ -135,7 +135,7 @@ extern "C" int pwqt_solve_noalloc(pwqt_ctx* c, int sys, int n_E, const double* E
     SweepSys sy{n, N, c->M0.as<double2>(), c->M1.as<double2>(), s.HV0.as<double2>(), s.HV1.as<double2>()};
     launch_sweep_fp64(sy, reinterpret_cast<const SweepJob*>(base + off_jobs), n_E, st);
     launch_observables(n, N, reinterpret_cast<const ObsJob*>(base + off_obs), n_E, st);
-    c->launches += 2;
+    c->launches += 3;   // sweep, observables, node densities
     PWQT_CUDA(c, cudaGetLastError());
     PWQT_CUDA(c, cudaStreamSynchronize(st));
     return PWQT_OK;

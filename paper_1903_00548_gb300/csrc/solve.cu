@@ -45,19 +45,6 @@ __global__ void k_observables(int n, int N, const ObsJob* __restrict__ jobs) {
     atomicAdd(&acc[0], t_loc);
     atomicAdd(&acc[1], r_loc);
     atomicAdd(&acc[2], tds_loc);
-    // node densities
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const double2* ci = J.C + (size_t)i * J.node_stride;
-        double ns = 0, nd = 0;
-        for (int r = 0; r < n; ++r)
-            for (int g = 0; g < m; ++g) {
-                double v = cnorm2(ci[(size_t)r * J.row_stride + g]);
-                if (g < J.ms) ns += v * 2.0 / J.v_in_s[g];
-                else nd += v * 2.0 / J.v_in_d[g - J.ms];
-            }
-        J.node_n[2 * i] = ns;
-        J.node_n[2 * i + 1] = nd;
-    }
     __syncthreads();
     if (threadIdx.x == 0) {
         *J.T = acc[0];
@@ -66,8 +53,44 @@ __global__ void k_observables(int n, int N, const ObsJob* __restrict__ jobs) {
     }
 }
 
+// node density of node blockIdx.x, energy blockIdx.y: one CTA sums the n x m
+// coefficients of the node with the per-mode weights 2/|v| and reduces in the block
+constexpr int MAXW = 2048;   // injected modes per energy held in shared memory (m <= 2n <= 2048)
+__global__ void __launch_bounds__(256) k_node_density(int n, const ObsJob* __restrict__ jobs) {
+    const ObsJob J = jobs[blockIdx.y];
+    const int m = J.ms + J.md, i = blockIdx.x;
+    __shared__ double wgt[MAXW];
+    __shared__ double red[2][8];
+    for (int g = threadIdx.x; g < m; g += blockDim.x)
+        wgt[g] = g < J.ms ? 2.0 / J.v_in_s[g] : 2.0 / J.v_in_d[g - J.ms];
+    __syncthreads();
+    double ns = 0, nd = 0;
+    if (m > 0) {
+        const double2* ci = J.C + (size_t)i * J.node_stride;
+        for (int t = threadIdx.x; t < n * m; t += blockDim.x) {
+            const int r = t / m, g = t % m;
+            const double v = cnorm2(ci[(size_t)r * J.row_stride + g]) * wgt[g];
+            if (g < J.ms) ns += v;
+            else nd += v;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ns += __shfl_down_sync(0xffffffffu, ns, o);
+        nd += __shfl_down_sync(0xffffffffu, nd, o);
+    }
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = ns; red[1][threadIdx.x >> 5] = nd; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0;
+        for (int q = 0; q < 8; ++q) { a += red[0][q]; b += red[1][q]; }
+        J.node_n[2 * i] = a;
+        J.node_n[2 * i + 1] = b;
+    }
+}
+
 void launch_observables(int n, int N, const ObsJob* jobs, int nb, cudaStream_t st) {
     k_observables<<<nb, 256, 0, st>>>(n, N, jobs);
+    k_node_density<<<dim3(N, nb), 256, 0, st>>>(n, jobs);
 }
 
 // ---------------------------------------------------------------- FP64 residual
@@ -277,7 +300,7 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
             }
         }
         launch_observables(n, N, obs_d.as<ObsJob>(), nb, st);
-        c->launches++;
+        c->launches += 2;
         PWQT_CUDA(c, cudaGetLastError());
         if (dens) {
             DensityAcc d = *dens;

@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
     float2* XY = S.XY + e * S.sXY + (size_t)i * n * w;
     int* piv = S.piv + e * S.sP + (size_t)i * n;
     int st = 0;
+#pragma unroll 8
     for (int t = threadIdx.x; t < rows * PW; t += NT) {
         int r = t / PW, c = t % PW;
         P[t] = c < wd ? F[(size_t)(k0 + r) * n + k0 + c] : make_float2(0.f, 0.f);
@@ -166,27 +167,53 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
         }
         __syncthreads();
     }
+#pragma unroll 8
     for (int t = threadIdx.x; t < rows * wd; t += NT) {
         int r = t / wd, c = t % wd;
         F[(size_t)(k0 + r) * n + k0 + c] = P[r * PW + c];
     }
-    // row interchanges on the other columns of F_i and on XY_i, in order; every
-    // thread owns whole columns, so the swaps need no barrier between them
+    // row interchanges on the other columns of F_i and on XY_i: the wd swaps in order
+    // compose to a permutation of at most 2 wd panel rows, moved as one gather per
+    // column (all loads of a column issued before its stores)
+    __shared__ int mv_dst[2 * PW], mv_src[2 * PW], mv_cnt;
+    if (threadIdx.x == 0) {
+        int pos[2 * PW], cur[2 * PW], cnt = 0;   // panel rows touched and the original row now there
+        auto slot = [&](int r) {
+            for (int q = 0; q < cnt; ++q)
+                if (pos[q] == r) return q;
+            pos[cnt] = r;
+            cur[cnt] = r;
+            return cnt++;
+        };
+        for (int j = 0; j < wd; ++j) {
+            const int p = prow[j];
+            if (p == j) continue;
+            const int a = slot(j), b = slot(p);
+            const int x = cur[a];
+            cur[a] = cur[b];
+            cur[b] = x;
+        }
+        int k = 0;
+        for (int q = 0; q < cnt; ++q)
+            if (cur[q] != pos[q]) { mv_dst[k] = pos[q]; mv_src[k] = cur[q]; ++k; }
+        mv_cnt = k;
+    }
+    __syncthreads();
+    const int nmv = mv_cnt;
     const int ncolF = n - wd;
     for (int c = threadIdx.x; c < ncolF + w; c += NT) {
         float2* base;
         size_t ld;
         if (c < ncolF) { base = F + (c < k0 ? c : c + wd); ld = n; }
         else { base = XY + (c - ncolF); ld = w; }
-        for (int j = 0; j < wd; ++j) {
-            const int p = prow[j];
-            if (p == j) continue;
-            float2* a = base + (size_t)(k0 + j) * ld;
-            float2* b = base + (size_t)(k0 + p) * ld;
-            const float2 x = *a;
-            *a = *b;
-            *b = x;
-        }
+        base += (size_t)k0 * ld;
+        float2 v[2 * PW];
+#pragma unroll
+        for (int q = 0; q < 2 * PW; ++q)
+            if (q < nmv) v[q] = base[(size_t)mv_src[q] * ld];
+#pragma unroll
+        for (int q = 0; q < 2 * PW; ++q)
+            if (q < nmv) base[(size_t)mv_dst[q] * ld] = v[q];
     }
     __syncthreads();
     // strip: rows k0..k0+wd of [F cols k0+wd..n | XY] <- L11^{-1} strip (unit lower)
@@ -308,9 +335,18 @@ __device__ __forceinline__ void lu_offdiag(const float2* __restrict__ F, int n, 
     const int t = threadIdx.x;
     for (int rc = r_begin; rc < r_end; rc += LR) {
         const int rows = min(LR, r_end - rc);
-        for (int q = t; q < LR * PW; q += NT) {
-            const int rr = q / PW, l = q % PW;
-            Fs[rr * (PW + 1) + l] = (rr < rows && l < wd) ? F[(size_t)(rc + rr) * n + kb + l] : make_float2(0.f, 0.f);
+        // one CTA per (energy, column group) leaves little to hide memory latency:
+        // issue all of this thread's loads before any store
+        float2 v[LR * PW / NT];
+#pragma unroll
+        for (int u = 0; u < LR * PW / NT; ++u) {
+            const int q = t + u * NT, rr = q / PW, l = q % PW;
+            v[u] = (rr < rows && l < wd) ? F[(size_t)(rc + rr) * n + kb + l] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < LR * PW / NT; ++u) {
+            const int q = t + u * NT;
+            Fs[(q / PW) * (PW + 1) + q % PW] = v[u];
         }
         __syncthreads();
         for (int q = t; q < rows * LC; q += NT) {
@@ -351,6 +387,7 @@ __global__ void __launch_bounds__(NT) k_mx_lusolve(MixSys S, int i, const int* _
         }
     }
     __syncthreads();
+#pragma unroll 8
     for (int q = t; q < n * LC; q += NT) {
         const int r = q / LC, g = q % LC;
         T[q] = c0 + g < m ? W[(size_t)perm[r] * w + c0 + g] : make_float2(0.f, 0.f);
@@ -359,9 +396,18 @@ __global__ void __launch_bounds__(NT) k_mx_lusolve(MixSys S, int i, const int* _
     // forward substitution, unit lower factor
     for (int kb = 0; kb < n; kb += PW) {
         const int wd = min(PW, n - kb);
-        for (int q = t; q < PW * PW; q += NT) {
-            const int r = q / PW, c = q % PW;
-            Ld[r * (PW + 1) + c] = (r < wd && c < wd) ? F[(size_t)(kb + r) * n + kb + c] : make_float2(0.f, 0.f);
+        {
+            float2 v[PW * PW / NT];
+#pragma unroll
+            for (int u = 0; u < PW * PW / NT; ++u) {
+                const int q = t + u * NT, r = q / PW, c = q % PW;
+                v[u] = (r < wd && c < wd) ? F[(size_t)(kb + r) * n + kb + c] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < PW * PW / NT; ++u) {
+                const int q = t + u * NT;
+                Ld[(q / PW) * (PW + 1) + q % PW] = v[u];
+            }
         }
         __syncthreads();
         for (int cc = 2 * warp; cc < 2 * warp + 2; ++cc) {
@@ -381,9 +427,18 @@ __global__ void __launch_bounds__(NT) k_mx_lusolve(MixSys S, int i, const int* _
     // backward substitution, upper factor with its diagonal
     for (int kb = ((n - 1) / PW) * PW; kb >= 0; kb -= PW) {
         const int wd = min(PW, n - kb);
-        for (int q = t; q < PW * PW; q += NT) {
-            const int r = q / PW, c = q % PW;
-            Ld[r * (PW + 1) + c] = (r < wd && c < wd) ? F[(size_t)(kb + r) * n + kb + c] : make_float2(r == c ? 1.f : 0.f, 0.f);
+        {
+            float2 v[PW * PW / NT];
+#pragma unroll
+            for (int u = 0; u < PW * PW / NT; ++u) {
+                const int q = t + u * NT, r = q / PW, c = q % PW;
+                v[u] = (r < wd && c < wd) ? F[(size_t)(kb + r) * n + kb + c] : make_float2(r == c ? 1.f : 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < PW * PW / NT; ++u) {
+                const int q = t + u * NT;
+                Ld[(q / PW) * (PW + 1) + q % PW] = v[u];
+            }
         }
         __syncthreads();
         for (int cc = 2 * warp; cc < 2 * warp + 2; ++cc) {
