@@ -39,6 +39,7 @@ typedef struct pwqt_ctx pwqt_ctx;
 #define PWQT_ERR_CUDA            -4   /* a CUDA runtime / library call failed      */
 #define PWQT_ERR_STATE           -5   /* call order violated (e.g. no basis yet)   */
 #define PWQT_ERR_NO_DEVICE       -6   /* no CUDA device / driver                   */
+#define PWQT_ERR_TIMEOUT         -7   /* a bounded device-side wait gave up        */
 
 /* per-result status bits (pwqt_solve `status` output) */
 #define PWQT_ST_OK               0
@@ -52,7 +53,9 @@ typedef struct pwqt_ctx pwqt_ctx;
 #define PWQT_FP64                0    /* complex128 throughout                     */
 #define PWQT_MIXED               1    /* complex64 factorisation on the tensor
                                          cores (3xTF32 products, FP32 accumulate)
-                                         + refinement with FP64 residuals          */
+                                         + refinement with float-float residuals   */
+#define PWQT_FP32                2    /* the complex64 factorisation alone (no
+                                         refinement; resid reports its residual)   */
 
 typedef struct {
     int    device;             /* CUDA device ordinal                              */
@@ -158,6 +161,17 @@ int pwqt_set_extrinsic(pwqt_ctx* ctx, int sys, int n_nodes, const double* U_node
 int pwqt_solve(pwqt_ctx* ctx, int sys, int n_E, const double* E, int precision,
                double* T, double* R, double* T_ds, int* n_open, double* node_n,
                double* resid, int* iters, int* status);
+
+/*
+ * pwqt_solve for several systems (e.g. bias points of one device) at the same n_E
+ * energies: results are system-major, entry s * n_E + e for system sys_ids[s];
+ * node_n holds n_E * N_s * 2 values per system, systems back to back in the
+ * order given.  Errors: as pwqt_solve (nothing is written past the first failing
+ * system's block).
+ */
+int pwqt_solve_multi(pwqt_ctx* ctx, int n_sys, const int* sys_ids, int n_E, const double* E, int precision,
+                     double* T, double* R, double* T_ds, int* n_open, double* node_n,
+                     double* resid, int* iters, int* status);
 
 /*
  * pwqt_solve on device buffers: E (n_E doubles) and every output are device

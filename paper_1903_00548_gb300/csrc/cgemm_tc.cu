@@ -38,6 +38,7 @@ constexpr uint32_t SBO = (BKR * 4 / 16) * CORE_BYTES;   // next 8-row group: 16 
 constexpr uint32_t A_BYTES = BM * BKR * 4;           // 32 KB
 constexpr uint32_t B_BYTES = BNR * BKR * 4;          // 64 KB
 constexpr uint32_t SMEM_BYTES = 2 * A_BYTES + 2 * B_BYTES + 64;
+static_assert(sizeof(float) * BM * (BNR + 1) <= 2 * A_BYTES + 2 * B_BYTES, "epilogue tile fits the stage buffers");
 constexpr uint32_t TMEM_COLS = 256;
 constexpr long long SPIN_LIMIT = 1ll << 22;   // bounded mbarrier polling (each poll returns within microseconds)
 
@@ -184,8 +185,10 @@ k_cgemm_tc(const CGemmArgs G, int M, int N, int K) {
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(smem_u32(mbar)));
         }
-        // the next stage overwrites shared memory: wait until the MMAs have read it
+        // the next stage overwrites shared memory: wait until the MMAs have read it; the
+        // block agrees on the outcome, so every barrier below is reached by all threads
         ok = mbar_wait(smem_u32(mbar), phase);
+        ok = __syncthreads_and(ok) != 0;
         phase ^= 1u;
         if (ok) {
             asm volatile("tcgen05.fence::after_thread_sync;");
@@ -205,19 +208,24 @@ k_cgemm_tc(const CGemmArgs G, int M, int N, int K) {
         if (tid == 0) atomicExch(&g_tc_error, 1);
         mbar_wait(smem_u32(mbar), phase ^ 1u);   // bounded second wait for the MMAs in flight
     } else {
-        // ---- epilogue: C -= acc; this thread owns tile row (warp % 4) * 32 + lane, columns colhalf..+128
-        const int r = row0 + (warp & 3) * 32 + (tid & 31);
-        if (r < M) {
+        // ---- epilogue: C -= acc.  A thread holds one tile row ((warp % 4) * 32 + lane) and 128
+        // real columns; the tile goes through shared memory (rows padded to an odd stride, so
+        // the row-per-lane writes are conflict-free) and C is then read and written along rows,
+        // consecutive threads on consecutive columns.
+        float* tile = reinterpret_cast<float*>(smem);   // BM x (BNR + 1); the stage buffers are free now
+        constexpr int TS = BNR + 1;
+        const int lr = (warp & 3) * 32 + (tid & 31);
 #pragma unroll
-            for (int j = 0; j < 64; ++j) {
-                const int cc = col0 + colhalf / 2 + j;
-                if (cc < N) {
-                    float2* p = cc < J.split ? J.C1 + (size_t)r * J.ldc1 + cc : J.C2 + (size_t)r * J.ldc2 + (cc - J.split);
-                    float2 o = *p;
-                    o.x -= acc[2 * j];
-                    o.y -= acc[2 * j + 1];
-                    *p = o;
-                }
+        for (int j = 0; j < 128; ++j) tile[lr * TS + colhalf + j] = acc[j];
+        __syncthreads();
+        for (int q = tid; q < BM * BNC; q += THREADS) {
+            const int rr = q / BNC, cl = q % BNC, r = row0 + rr, cc = col0 + cl;
+            if (r < M && cc < N) {
+                float2* p = cc < J.split ? J.C1 + (size_t)r * J.ldc1 + cc : J.C2 + (size_t)r * J.ldc2 + (cc - J.split);
+                float2 o = *p;
+                o.x -= tile[rr * TS + 2 * cl];
+                o.y -= tile[rr * TS + 2 * cl + 1];
+                *p = o;
             }
         }
     }

@@ -25,7 +25,8 @@ int solve_common(pwqt_ctx* c, int sys, int n_E, const double* E, int precision, 
     if (!c->n) return fail(c, PWQT_ERR_STATE, "no basis: call pwqt_assemble_intrinsic first");
     auto it = c->systems.find(sys);
     if (it == c->systems.end()) return fail(c, PWQT_ERR_STATE, "unknown system: call pwqt_set_extrinsic first");
-    if (precision != PWQT_FP64 && precision != PWQT_MIXED) return fail(c, PWQT_ERR_INVALID_ARG, "bad precision");
+    if (precision != PWQT_FP64 && precision != PWQT_MIXED && precision != PWQT_FP32)
+        return fail(c, PWQT_ERR_INVALID_ARG, "bad precision");
     if (n_E < 0 || (n_E > 0 && !E)) return fail(c, PWQT_ERR_INVALID_ARG, "bad energies");
     if (c->n > 1024) return fail(c, PWQT_ERR_INVALID_ARG, "block size above 1024");
     for (int e = 0; e < n_E; ++e)
@@ -373,6 +374,24 @@ int pwqt_set_refinement(pwqt_ctx* c, double ir_tol, int ir_max_iters) {
         return fail(c, PWQT_ERR_INVALID_ARG, "ir_tol must be finite and >= 0, ir_max_iters >= 0");
     c->opts.ir_tol = ir_tol > 0 ? ir_tol : 1e-9;
     c->opts.ir_max_iters = ir_max_iters > 0 ? ir_max_iters : 40;
+    return PWQT_OK;
+}
+
+
+int pwqt_solve_multi(pwqt_ctx* c, int n_sys, const int* sys_ids, int n_E, const double* E, int precision, double* T, double* R,
+                     double* T_ds, int* n_open, double* node_n, double* resid, int* iters, int* status) {
+    PWQT_TRY(check_ctx(c));
+    if (n_sys < 0 || (n_sys > 0 && !sys_ids)) return fail(c, PWQT_ERR_INVALID_ARG, "bad system list");
+    size_t nn_off = 0;
+    for (int q = 0; q < n_sys; ++q) {
+        auto it = c->systems.find(sys_ids[q]);
+        if (it == c->systems.end()) return fail(c, PWQT_ERR_STATE, "unknown system in the list");
+        const size_t o = (size_t)q * n_E;
+        PWQT_TRY(pwqt_solve(c, sys_ids[q], n_E, E, precision, T ? T + o : nullptr, R ? R + o : nullptr, T_ds ? T_ds + o : nullptr,
+                            n_open ? n_open + 2 * o : nullptr, node_n ? node_n + nn_off : nullptr, resid ? resid + o : nullptr,
+                            iters ? iters + o : nullptr, status ? status + o : nullptr));
+        nn_off += (size_t)n_E * it->second.N * 2;
+    }
     return PWQT_OK;
 }
 

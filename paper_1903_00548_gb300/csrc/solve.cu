@@ -190,7 +190,7 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
     size_t budget = c->opts.hbm_budget_bytes ? c->opts.hbm_budget_bytes : (size_t)(0.85 * (double)free_b);
     auto per_energy = [&](int e) {
         int m = ms[e] + md[e];
-        if (precision == PWQT_MIXED) return mixed_bytes_per_energy(n, N, std::max(m, 1)) + 64 * sizeof(double) * (m + 2);
+        if (precision != PWQT_FP64) return mixed_bytes_per_energy(n, N, std::max(m, 1)) + 64 * sizeof(double) * (m + 2);
         return sizeof(double2) * ((size_t)N * n * (n + m) + nn) + 64 * sizeof(double) * (m + 2);
     };
     SweepSys sys{n, N, c->M0.as<double2>(), c->M1.as<double2>(), s.HV0.as<double2>(), s.HV1.as<double2>()};
@@ -220,7 +220,7 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
         size_t maxm = 1;
         for (int b = 0; b < nb; ++b) maxm = std::max<size_t>(maxm, ms[e0 + b] + md[e0 + b]);
         DBuf &XY = c->ws_xy, &Sb = c->ws_s, &jobs_d = c->ws_jobs, &obs_d = c->ws_obs, &res_d = c->ws_res, &norms = c->ws_norms;
-        if (precision != PWQT_MIXED) {
+        if (precision == PWQT_FP64) {
             PWQT_TRY(ensure(c, XY, sizeof(double2) * std::max<size_t>(off[nb], 1)));
             PWQT_TRY(ensure(c, Sb, sizeof(double2) * nn * nb));
         }
@@ -242,8 +242,8 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
             J.sig_d = bad ? zero : Ld->sigma_d.as<double2>();
             J.rhs_s = bad ? zero : Ls->rhs_s.as<double2>();
             J.rhs_d = bad ? zero : Ld->rhs_d.as<double2>();
-            J.XY = precision == PWQT_MIXED ? nullptr : XY.as<double2>() + off[b];
-            J.S = precision == PWQT_MIXED ? nullptr : Sb.as<double2>() + nn * b;
+            J.XY = precision != PWQT_FP64 ? nullptr : XY.as<double2>() + off[b];
+            J.S = precision != PWQT_FP64 ? nullptr : Sb.as<double2>() + nn * b;
             J.status = o.status + e;
             ObsJob& O = obs[b];
             O.ms = ms[e]; O.md = md[e];
@@ -275,9 +275,9 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
         PWQT_CUDA(c, cudaMemcpyAsync(jobs_d.p, jobs.data(), sizeof(SweepJob) * nb, cudaMemcpyHostToDevice, st));
         PWQT_CUDA(c, cudaMemcpyAsync(obs_d.p, obs.data(), sizeof(ObsJob) * nb, cudaMemcpyHostToDevice, st));
         PWQT_CUDA(c, cudaMemcpyAsync(res_d.p, res.data(), sizeof(ResJob) * nb, cudaMemcpyHostToDevice, st));
-        if (precision == PWQT_MIXED) {
+        if (precision != PWQT_FP64) {
             PWQT_TRY(solve_mixed(c, s, sys, jobs, jobs_d.as<SweepJob>(), res, res_d.as<ResJob>(), obs, obs_d.as<ObsJob>(), nb,
-                                 o.iters + e0, st));
+                                 o.iters + e0, st, precision == PWQT_MIXED));
         } else {
             if (c->profile) PWQT_CUDA(c, cudaEventRecord(c->ev0, st));
             launch_sweep_fp64(sys, jobs_d.as<SweepJob>(), nb, st);

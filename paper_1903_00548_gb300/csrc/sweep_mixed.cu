@@ -496,7 +496,7 @@ size_t mixed_bytes_per_energy(int n, int N, int m) {
 }
 
 int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJob>& jobs, SweepJob* jobs_d, std::vector<ResJob>& res,
-                ResJob* res_d, std::vector<ObsJob>& obs, ObsJob* obs_d, int nb, int* iters_dev, cudaStream_t st) {
+                ResJob* res_d, std::vector<ObsJob>& obs, ObsJob* obs_d, int nb, int* iters_dev, cudaStream_t st, bool refine) {
     static bool inited = false;
     if (!inited) {
         if (cgemm_tc_init() != 0) return fail(c, PWQT_ERR_CUDA, "tensor-core GEMM set-up failed");
@@ -588,7 +588,7 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         c->prof_flops += (56.0 / 3.0) * (double)N * n * n * (double)n * nb;
     }
     PWQT_CUDA(c, cudaGetLastError());
-    if (cgemm_tc_error(true)) return fail(c, PWQT_ERR_CUDA, "tensor-core GEMM wait timed out");
+    if (cgemm_tc_error(true)) return fail(c, PWQT_ERR_TIMEOUT, "tensor-core GEMM: a bounded mbarrier wait gave up");
     k_mx_to64<<<dim3(256, nb), NT, 0, st>>>(S);
     c->launches++;
 
@@ -629,7 +629,7 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         int any = 0;
         for (int b = 0; b < nb; ++b) {
             if (!active[b]) continue;
-            if (resid[b] <= tol) { active[b] = 0; continue; }
+            if (!refine || resid[b] <= tol) { active[b] = 0; continue; }   // PWQT_FP32: report, do not refine
             if (resid[b] > 0.5 * prev[b]) stall[b]++;
             else stall[b] = 0;
             // a residual that stops falling within 10 ir_tol has met the accuracy floor of

@@ -16,15 +16,16 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpwqt.so")
 
 PWQT_OK = 0
-ERR_NAMES = {-1: "INVALID_ARG", -2: "BASIS_TOO_SMALL", -3: "OOM", -4: "CUDA", -5: "STATE", -6: "NO_DEVICE"}
-FP64, MIXED = 0, 1
+ERR_NAMES = {-1: "INVALID_ARG", -2: "BASIS_TOO_SMALL", -3: "OOM", -4: "CUDA", -5: "STATE", -6: "NO_DEVICE",
+             -7: "TIMEOUT"}
+FP64, MIXED, FP32 = 0, 1, 2
 ST_SINGULAR_PIVOT, ST_MODE_COUNT, ST_IR_NO_CONVERGE, ST_DEGENERATE, ST_NEAR_UNIT = 1, 2, 4, 8, 16
 
 EXPORTS = ["pwqt_create", "pwqt_destroy", "pwqt_last_error", "pwqt_assemble_intrinsic", "pwqt_set_enhancement",
            "pwqt_get_blocks", "pwqt_set_extrinsic", "pwqt_solve", "pwqt_solve_dev", "pwqt_prepare_leads",
            "pwqt_cache_info", "pwqt_bands", "pwqt_kernel_launches", "pwqt_profile", "pwqt_solve_noalloc", "pwqt_cgemm_c64",
            "pwqt_density_reset", "pwqt_accumulate_density", "pwqt_get_density_matrix", "pwqt_density_grid",
-           "pwqt_profile_refinement", "pwqt_set_refinement"]
+           "pwqt_profile_refinement", "pwqt_set_refinement", "pwqt_solve_multi"]
 
 
 class PwqtError(RuntimeError):
@@ -79,6 +80,7 @@ def load(path: str = LIB_PATH):
     lib.pwqt_density_reset.argtypes = [P, I]
     lib.pwqt_profile_refinement.argtypes = [P, dp, dp, C.POINTER(C.c_longlong)]
     lib.pwqt_set_refinement.argtypes = [P, D, I]
+    lib.pwqt_solve_multi.argtypes = [P, I, ip, I, dp, I, dp, dp, dp, ip, dp, dp, ip, ip]
     lib.pwqt_accumulate_density.argtypes = [P, I, I, dp, dp, D, D, D, I, ip]
     lib.pwqt_get_density_matrix.argtypes = [P, I, dp, dp]
     lib.pwqt_density_grid.argtypes = [P, I, I, I, dp]
@@ -217,6 +219,27 @@ class Context:
         self._check(self.lib.pwqt_solve(self.h, sys, nE, _dptr(E), precision, _dptr(T), _dptr(R), _dptr(Tds), _iptr(nopen),
                                         _dptr(node_n), _dptr(resid), _iptr(iters), _iptr(status)))
         return SolveResult(T, R, Tds, nopen, node_n, resid, iters, status)
+
+    def solve_multi(self, systems, E, precision: int = FP64):
+        """pwqt_solve_multi: one SolveResult per system (node_n shaped by each system's node count)."""
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        ids = np.ascontiguousarray(systems, dtype=np.int32)
+        nS, nE = len(ids), len(E)
+        Ns = [self.n_nodes.get(int(q), 0) for q in ids]
+        T, R, Tds, resid = (np.zeros(nS * nE) for _ in range(4))
+        nopen = np.zeros((nS * nE, 2), np.int32)
+        node_n = np.zeros(sum(nE * N * 2 for N in Ns))
+        iters = np.zeros(nS * nE, np.int32)
+        status = np.zeros(nS * nE, np.int32)
+        self._check(self.lib.pwqt_solve_multi(self.h, nS, _iptr(ids), nE, _dptr(E), precision, _dptr(T), _dptr(R), _dptr(Tds),
+                                              _iptr(nopen), _dptr(node_n), _dptr(resid), _iptr(iters), _iptr(status)))
+        out, off = [], 0
+        for q, N in enumerate(Ns):
+            sl = slice(q * nE, (q + 1) * nE)
+            nn = node_n[off: off + nE * N * 2].reshape(nE, N, 2)
+            off += nE * N * 2
+            out.append(SolveResult(T[sl], R[sl], Tds[sl], nopen[sl], nn, resid[sl], iters[sl], status[sl]))
+        return out
 
     def solve_dev(self, sys: int, E, precision: int, out: dict, stream_ptr: int = 0):
         """Device-buffer variant: `out` maps output names to device pointers (int) or None."""

@@ -274,3 +274,25 @@ def test_refinement_settings(pw, chain):
     assert np.all(d.status == 0) and np.all(d.resid <= 1e-8)
     with pytest.raises(pw.PwqtError):
         ctx.set_refinement(-1.0, 0)
+
+
+def test_fp32_precision_and_multi_system_solve(pw, chain):
+    # PWQT_FP32: the complex64 factorisation alone (no refinement) is within its own
+    # residual of the FP64 answer; pwqt_solve_multi equals per-system solves
+    wl, s = chain
+    ctx = _ctx_with_basis(pw, s)
+    ctx.set_extrinsic(0, wl.U)
+    ctx.set_extrinsic(1, np.zeros_like(wl.U))
+    E = wl.energies[8:16]
+    r64 = ctx.solve(0, E, pw.FP64)
+    r32 = ctx.solve(0, E, pw.FP32)
+    assert np.all(r32.iters == 0) and np.all(r32.status & pw.ST_IR_NO_CONVERGE == 0)
+    assert np.all(r32.resid < 1e-3)
+    assert np.max(np.abs(r32.T - r64.T)) < 1e-3 * max(1.0, np.max(r64.T))
+    multi = ctx.solve_multi([1, 0], E, pw.FP64)
+    one = ctx.solve(1, E, pw.FP64)
+    # the observables reduce with shared-memory atomics: equal up to summation order
+    assert np.allclose(multi[1].T, r64.T, rtol=1e-13, atol=1e-13) and np.allclose(multi[0].T, one.T, rtol=1e-13, atol=1e-13)
+    assert np.allclose(multi[1].node_n, r64.node_n, rtol=1e-13, atol=0)
+    # pristine system: integer transmission
+    assert np.all(np.abs(one.T - np.round(one.T)) < 1e-8)
