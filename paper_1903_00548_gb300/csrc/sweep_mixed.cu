@@ -101,12 +101,15 @@ __global__ void k_mx_form(MixSys S, int i, int only_L) {
 // interchanges to the remaining columns of F_i and to XY_i, and solve the unit-lower
 // 32 x 32 block against the strip rows k0..k0+wd of [F_i right of the panel | XY_i].
 __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd) {
-    extern __shared__ float2 P[];                     // (n - k0) x PW panel
+    // the panel, column-major with an odd leading dimension: threads walk rows of one
+    // column (consecutive words) in the elimination and columns of one row (odd stride,
+    // distinct banks) when it is loaded and stored
+    extern __shared__ float2 P[];                     // PW columns x ld rows
     __shared__ int prow[PW];
     __shared__ float bv[NT / 32];
     __shared__ int bi[NT / 32];
     const int e = blockIdx.x;
-    const int n = S.n, w = S.w, rows = n - k0;
+    const int n = S.n, w = S.w, rows = n - k0, ld = rows | 1;
     float2* F = S.F + e * S.sF + (size_t)i * n * n;
     float2* XY = S.XY + e * S.sXY + (size_t)i * n * w;
     int* piv = S.piv + e * S.sP + (size_t)i * n;
@@ -114,7 +117,7 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
 #pragma unroll 8
     for (int t = threadIdx.x; t < rows * PW; t += NT) {
         int r = t / PW, c = t % PW;
-        P[t] = c < wd ? F[(size_t)(k0 + r) * n + k0 + c] : make_float2(0.f, 0.f);
+        P[c * ld + r] = c < wd ? F[(size_t)(k0 + r) * n + k0 + c] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     // pivot candidates of column 0; afterwards each elimination pass also finds the
@@ -122,7 +125,7 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
     float best = -1.f;
     int idx = 0;
     for (int r = threadIdx.x; r < rows; r += NT) {
-        const float2 v = P[r * PW];
+        const float2 v = P[r];
         const float a = fabsf(v.x) + fabsf(v.y);
         if (a > best) { best = a; idx = r; }
     }
@@ -144,23 +147,23 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
         __syncthreads();
         const int p = prow[j];
         if (p != j && threadIdx.x < PW) {
-            float2 a = P[j * PW + threadIdx.x];
-            P[j * PW + threadIdx.x] = P[p * PW + threadIdx.x];
-            P[p * PW + threadIdx.x] = a;
+            float2 a = P[threadIdx.x * ld + j];
+            P[threadIdx.x * ld + j] = P[threadIdx.x * ld + p];
+            P[threadIdx.x * ld + p] = a;
         }
         __syncthreads();
-        float2 pv = P[j * PW + j];
+        float2 pv = P[j * ld + j];
         if (pv.x == 0.f && pv.y == 0.f) { st |= PWQT_ST_SINGULAR_PIVOT; pv = make_float2(1.f, 0.f); }
         const float2 inv = fdiv(make_float2(1.f, 0.f), pv);
         best = -1.f;
         idx = j + 1;
         for (int r = j + 1 + threadIdx.x; r < rows; r += NT) {
-            const float2 x = P[r * PW + j];
+            const float2 x = P[j * ld + r];
             const float2 l = make_float2(x.x * inv.x - x.y * inv.y, x.x * inv.y + x.y * inv.x);
-            P[r * PW + j] = l;
-            for (int c = j + 1; c < wd; ++c) ffma(P[r * PW + c], make_float2(-l.x, -l.y), P[j * PW + c]);
+            P[j * ld + r] = l;
+            for (int c = j + 1; c < wd; ++c) ffma(P[c * ld + r], make_float2(-l.x, -l.y), P[c * ld + j]);
             if (j + 1 < wd) {
-                const float2 v = P[r * PW + j + 1];
+                const float2 v = P[(j + 1) * ld + r];
                 const float a = fabsf(v.x) + fabsf(v.y);
                 if (a > best) { best = a; idx = r; }
             }
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
 #pragma unroll 8
     for (int t = threadIdx.x; t < rows * wd; t += NT) {
         int r = t / wd, c = t % wd;
-        F[(size_t)(k0 + r) * n + k0 + c] = P[r * PW + c];
+        F[(size_t)(k0 + r) * n + k0 + c] = P[c * ld + r];
     }
     // row interchanges on the other columns of F_i and on XY_i: the wd swaps in order
     // compose to a permutation of at most 2 wd panel rows, moved as one gather per
@@ -233,7 +236,7 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
 #pragma unroll
                 for (int l = 0; l < PW; ++l)
                     if (l < j) {
-                        float2 L = P[j * PW + l];
+                        float2 L = P[l * ld + j];
                         ffma(s, make_float2(-L.x, -L.y), x[l]);
                     }
                 x[j] = s;
@@ -379,10 +382,15 @@ __global__ void __launch_bounds__(NT) k_mx_lusolve(MixSys S, int i, const int* _
     const int* piv = S.piv + e * S.sP + (size_t)i * n;
     float2* W = S.XY + e * S.sXY + (size_t)i * n * w + n;     // row stride w
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // compose the pivots into a permutation: stage them in shared memory (T is free
+    // until it is loaded below) so the serial composition reads no global memory
+    int* pv = reinterpret_cast<int*>(T);
+    for (int j = t; j < n; j += NT) pv[j] = piv[j];
+    __syncthreads();
     if (t == 0) {
         for (int j = 0; j < n; ++j) perm[j] = j;
         for (int j = 0; j < n; ++j) {
-            int p = piv[j];
+            const int p = pv[j];
             if (p != j) { int a = perm[j]; perm[j] = perm[p]; perm[p] = a; }
         }
     }
@@ -536,7 +544,13 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
 
     // ---------------- forward sweep over the nodes
     const int fblocks = (int)std::min<size_t>(((size_t)n * n + NT - 1) / NT, 512);
-    const size_t panel_smem = sizeof(float2) * (size_t)n * PW;
+    const size_t panel_smem = sizeof(float2) * (size_t)(n + 1) * PW;
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev);
+    if (panel_smem > (size_t)smem_optin)
+        return fail(c, PWQT_ERR_INVALID_ARG, "the complex64 panel of block size " + std::to_string(n) +
+                                                 " exceeds shared memory: use PWQT_FP64 (mixed precision takes n <= " +
+                                                 std::to_string(smem_optin / (int)(sizeof(float2) * PW) - 1) + ")");
     if (panel_smem > 48 * 1024)
         PWQT_CUDA(c, cudaFuncSetAttribute(k_mx_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem));
     auto gemm = [&](const float2* A, long long sA, int lda, const float2* B1, long long sB1, int ldb1, const float2* B2, long long sB2,
@@ -557,7 +571,7 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         }
         for (int k0 = 0; k0 < n; k0 += PW) {
             const int wd = std::min(PW, n - k0);
-            k_mx_panel<<<nb, NT, sizeof(float2) * (size_t)(n - k0) * PW, st>>>(S, i, k0, wd);
+            k_mx_panel<<<nb, NT, sizeof(float2) * (size_t)((n - k0) | 1) * PW, st>>>(S, i, k0, wd);
             c->launches++;
             const int rest = n - k0 - wd;
             if (rest > 0)
