@@ -141,7 +141,8 @@ __global__ void k_residual_finish(const ResJob* __restrict__ jobs, int nb, const
     for (int g = 0; g < m; ++g) {
         double bb = J.bn2[g];
         double v = bb > 0 ? sqrt(J.rn2[g] / bb) : sqrt(J.rn2[g]);
-        worst = fmax(worst, v);
+        worst = (v > worst || isnan(v)) ? v : worst;   // NaN propagates (fmax would drop it)
+        if (isnan(worst)) break;
     }
     *J.resid = worst;
 }

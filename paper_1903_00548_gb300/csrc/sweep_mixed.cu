@@ -104,12 +104,12 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
     // the panel, column-major with an odd leading dimension: threads walk rows of one
     // column (consecutive words) in the elimination and columns of one row (odd stride,
     // distinct banks) when it is loaded and stored
-    extern __shared__ float2 P[];                     // PW columns x ld rows
+    extern __shared__ float2 P[];                     // PW columns x pld rows
     __shared__ int prow[PW];
     __shared__ float bv[NT / 32];
     __shared__ int bi[NT / 32];
     const int e = blockIdx.x;
-    const int n = S.n, w = S.w, rows = n - k0, ld = rows | 1;
+    const int n = S.n, w = S.w, rows = n - k0, pld = rows | 1;   // panel leading dimension (odd)
     float2* F = S.F + e * S.sF + (size_t)i * n * n;
     float2* XY = S.XY + e * S.sXY + (size_t)i * n * w;
     int* piv = S.piv + e * S.sP + (size_t)i * n;
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
 #pragma unroll 8
     for (int t = threadIdx.x; t < rows * PW; t += NT) {
         int r = t / PW, c = t % PW;
-        P[c * ld + r] = c < wd ? F[(size_t)(k0 + r) * n + k0 + c] : make_float2(0.f, 0.f);
+        P[c * pld + r] = c < wd ? F[(size_t)(k0 + r) * n + k0 + c] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     // pivot candidates of column 0; afterwards each elimination pass also finds the
@@ -147,23 +147,23 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
         __syncthreads();
         const int p = prow[j];
         if (p != j && threadIdx.x < PW) {
-            float2 a = P[threadIdx.x * ld + j];
-            P[threadIdx.x * ld + j] = P[threadIdx.x * ld + p];
-            P[threadIdx.x * ld + p] = a;
+            float2 a = P[threadIdx.x * pld + j];
+            P[threadIdx.x * pld + j] = P[threadIdx.x * pld + p];
+            P[threadIdx.x * pld + p] = a;
         }
         __syncthreads();
-        float2 pv = P[j * ld + j];
+        float2 pv = P[j * pld + j];
         if (pv.x == 0.f && pv.y == 0.f) { st |= PWQT_ST_SINGULAR_PIVOT; pv = make_float2(1.f, 0.f); }
         const float2 inv = fdiv(make_float2(1.f, 0.f), pv);
         best = -1.f;
         idx = j + 1;
         for (int r = j + 1 + threadIdx.x; r < rows; r += NT) {
-            const float2 x = P[j * ld + r];
+            const float2 x = P[j * pld + r];
             const float2 l = make_float2(x.x * inv.x - x.y * inv.y, x.x * inv.y + x.y * inv.x);
-            P[j * ld + r] = l;
-            for (int c = j + 1; c < wd; ++c) ffma(P[c * ld + r], make_float2(-l.x, -l.y), P[c * ld + j]);
+            P[j * pld + r] = l;
+            for (int c = j + 1; c < wd; ++c) ffma(P[c * pld + r], make_float2(-l.x, -l.y), P[c * pld + j]);
             if (j + 1 < wd) {
-                const float2 v = P[(j + 1) * ld + r];
+                const float2 v = P[(j + 1) * pld + r];
                 const float a = fabsf(v.x) + fabsf(v.y);
                 if (a > best) { best = a; idx = r; }
             }
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
 #pragma unroll 8
     for (int t = threadIdx.x; t < rows * wd; t += NT) {
         int r = t / wd, c = t % wd;
-        F[(size_t)(k0 + r) * n + k0 + c] = P[c * ld + r];
+        F[(size_t)(k0 + r) * n + k0 + c] = P[c * pld + r];
     }
     // row interchanges on the other columns of F_i and on XY_i: the wd swaps in order
     // compose to a permutation of at most 2 wd panel rows, moved as one gather per
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
 #pragma unroll
                 for (int l = 0; l < PW; ++l)
                     if (l < j) {
-                        float2 L = P[l * ld + j];
+                        float2 L = P[l * pld + j];
                         ffma(s, make_float2(-L.x, -L.y), x[l]);
                     }
                 x[j] = s;
@@ -643,6 +643,11 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         int any = 0;
         for (int b = 0; b < nb; ++b) {
             if (!active[b]) continue;
+            if (!std::isfinite(resid[b])) {   // a non-finite solution is not refined further
+                active[b] = 0;
+                bits[b] |= PWQT_ST_IR_NO_CONVERGE;
+                continue;
+            }
             if (!refine || resid[b] <= tol) { active[b] = 0; continue; }   // PWQT_FP32: report, do not refine
             if (resid[b] > 0.5 * prev[b]) stall[b]++;
             else stall[b] = 0;
