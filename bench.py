@@ -412,6 +412,101 @@ def run_ours(args, world, rank, local):
     return 0
 
 
+# ----------------------------------------------------------------------------- serving
+def run_serving(args, world, rank, local):
+    """Serving loop: a catalog of bases (block 64..512), requests with a random basis,
+    device length, energy count and precision, first submitted all at once (capacity),
+    then with Poisson arrivals at 70 % of that capacity (latency).  Energies come from
+    a fixed 48-point grid per basis whose contact self-energies are computed before
+    timing, as a serving deployment keeps them resident."""
+    import torch
+    from paper_1903_00548_gb300 import build as B
+    from paper_1903_00548_gb300 import pwqt as pw
+    from paper_1903_00548_gb300 import workloads as W
+
+    B.build()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    rib15 = W.armchair_ribbon_cell(W.ribbon_lines_for_width(1.5))
+    wl512 = W.ribbon512()
+    cat = {64: (rib15, W.FormFactor(), 45.0, 32), 128: (rib15, W.FormFactor(), 45.0, 64),
+           256: (rib15, W.FormFactor(), 45.0, 128), 512: (wl512.cell, wl512.ff, wl512.gcut, wl512.n_bands)}
+    # windows inside each basis' band range (its top band: ~10.6 eV at n = 64, ~21 eV at n = 128)
+    grids = {64: np.linspace(3.0, 4.0, 48), 128: np.linspace(10.0, 11.0, 48),
+             256: np.linspace(W.RIBBON15_G45_ECB - 0.05, W.RIBBON15_G45_ECB + 0.8, 48),
+             512: np.linspace(W.RIBBON13_G30_E64 - 0.05, W.RIBBON13_G30_E64 + 0.9, 48)}
+    srv = pw.Server(device=local)
+    t0 = time.perf_counter()
+    for nb in cat:
+        srv.add_basis(nb, *cat[nb])
+    # warm the contact caches (one short request per basis over its whole grid)
+    warm = [srv.submit(nb, np.zeros(4), grids[nb], pw.FP64) for nb in cat]
+    for t in warm:
+        srv.wait(t)
+    t_setup = time.perf_counter() - t0
+    rng = np.random.default_rng(7)
+    n_req = args.requests
+
+    def make():
+        out = []
+        for _ in range(n_req):
+            nb = int(2 ** rng.integers(6, 10))                    # block 64..512, log-uniform
+            N = int(rng.integers(50, 201))
+            nE = int(np.exp(rng.uniform(np.log(4), np.log(32))))   # 4..32 energies, log-uniform
+            E = np.sort(rng.choice(grids[nb], nE, replace=False))
+            prec = pw.FP32 if rng.random() < 0.5 else pw.MIXED
+            U = W.random_smooth(N, 0.3, int(rng.integers(1 << 30)))
+            out.append((nb, U, E, prec))
+        return out
+
+    # capacity: everything submitted at once
+    reqs = make()
+    srv.stats(reset=True)
+    t0 = time.perf_counter()
+    tickets = [srv.submit(*r) for r in reqs]
+    solves = 0
+    for t, r in zip(tickets, reqs):
+        res, _ = srv.wait(t)
+        solves += len(r[2])
+    t_cap = time.perf_counter() - t0
+    cap = solves / t_cap
+    req_rate = n_req / t_cap
+    # latency: Poisson arrivals at 70 % of the measured request rate
+    reqs = make()
+    srv.stats(reset=True)
+    gaps = rng.exponential(1.0 / (0.7 * req_rate), n_req)
+    t0 = time.perf_counter()
+    tickets = []
+    due = 0.0
+    for g, r in zip(gaps, reqs):
+        due += g
+        d = due - (time.perf_counter() - t0)
+        if d > 0:
+            time.sleep(d)
+        tickets.append(srv.submit(*r))
+    solves = 0
+    bad = 0
+    for t, r in zip(tickets, reqs):
+        res, _ = srv.wait(t)
+        solves += len(r[2])
+        bad += int(np.count_nonzero(res.status & ~(pw.ST_NEAR_UNIT | pw.ST_DEGENERATE)))
+    t_open = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    line = {"metric": "serving: energy-solves/s and p50/p99 request latency (mixed catalog)", "value": solves / t_open,
+            "unit": "energy-solves/s", "n_gpus": 1, "higher_is_better": True, "impl": "ours",
+            "latency_s": {"p50": st["p50_s"], "p99": st["p99_s"]}, "capacity_solves_per_s": cap,
+            "arrival_rate_req_per_s": 0.7 * req_rate, "requests": n_req, "bad_status": bad, "setup_s": t_setup,
+            "data": "synthetic",
+            "config": {"workload": "serving", "catalog_block_sizes": sorted(cat), "nodes": "U[50,200]",
+                       "energies_per_request": "log-uniform 4..32 from a 48-point grid per basis",
+                       "precision_mix": "50% complex64 alone (PWQT_FP32), 50% mixed + refinement",
+                       "arrivals": "Poisson at 70% of the measured closed-loop request rate, seed 7"}}
+    print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -424,10 +519,14 @@ def main(argv=None):
     ap.add_argument("--nodes", type=int, default=0, help="development only: shorter device")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-density", action="store_true", help="skip the density-matrix timing")
+    ap.add_argument("--serving", action="store_true", help="measure the serving loop instead of the headline metric")
+    ap.add_argument("--requests", type=int, default=60, help="requests per serving pass")
     args = ap.parse_args(argv)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.serving:
+        return run_serving(args, world, rank, local)
     return run_ours(args, world, rank, local)
 
 

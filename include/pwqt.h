@@ -39,7 +39,9 @@ typedef struct pwqt_ctx pwqt_ctx;
 #define PWQT_ERR_CUDA            -4   /* a CUDA runtime / library call failed      */
 #define PWQT_ERR_STATE           -5   /* call order violated (e.g. no basis yet)   */
 #define PWQT_ERR_NO_DEVICE       -6   /* no CUDA device / driver                   */
-#define PWQT_ERR_TIMEOUT         -7   /* a bounded device-side wait gave up        */
+#define PWQT_ERR_TIMEOUT         -7   /* a bounded wait gave up (device-side wait,
+                                         or pwqt_server_wait before completion)    */
+#define PWQT_ERR_BUSY            -8   /* the server's request queue is full        */
 
 /* per-result status bits (pwqt_solve `status` output) */
 #define PWQT_ST_OK               0
@@ -313,6 +315,76 @@ int pwqt_get_density_matrix(pwqt_ctx* ctx, int sys, double* rho_d, double* rho_u
  * density yet), PWQT_ERR_INVALID_ARG, PWQT_ERR_OOM.
  */
 int pwqt_density_grid(pwqt_ctx* ctx, int sys, int nx, int nz, double* n_r);
+
+/*
+ * Serving loop (continuous admission of solve requests).  A server owns one
+ * context per catalog basis, each with its own CUDA stream and host worker thread:
+ * requests on different bases run on the device at the same time, requests on one
+ * basis in arrival order.  A request starts when the estimated working sets of the
+ * running requests plus its own fit the device-memory budget; intrinsic blocks,
+ * the contact self-energy cache, factor workspaces and the last 8 potentials per
+ * basis stay resident between requests.  The paper has no serving layer; each
+ * request is the solve of Sec. 3.2-3.4 exactly as pwqt_solve_dev computes it.
+ */
+typedef struct pwqt_server pwqt_server;
+
+typedef struct {
+    int    device;             /* CUDA device ordinal                                  */
+    size_t hbm_budget_bytes;   /* admission budget; 0: 70 % of the free device memory  */
+    int    queue_capacity;     /* queued requests before submit returns BUSY; 0: 4096  */
+    double ir_tol;             /* as pwqt_opts                                         */
+    int    batch;              /* as pwqt_opts                                         */
+} pwqt_server_opts;
+
+typedef struct {
+    int           basis;       /* catalog id given to pwqt_server_add_basis           */
+    int           n_nodes;     /* N >= 2                                               */
+    const double* U;           /* N node potentials (eV), copied at submission         */
+    int           n_E;         /* >= 1                                                 */
+    const double* E;           /* energies (eV), copied at submission                  */
+    int           precision;   /* PWQT_FP64 | PWQT_MIXED | PWQT_FP32                   */
+    /* host outputs, caller-owned, written before pwqt_server_wait returns OK; each may
+       be NULL; sizes and meaning as pwqt_solve (node_n: n_E * N * 2)                  */
+    double *T, *R, *T_ds;
+    int*    n_open;
+    double* node_n;
+    double* resid;
+    int *   iters, *status;
+} pwqt_request;
+
+/* Errors: PWQT_ERR_NO_DEVICE, PWQT_ERR_INVALID_ARG (device ordinal), PWQT_ERR_CUDA. */
+int pwqt_server_create(pwqt_server** out, const pwqt_server_opts* opts);
+
+/* Add a catalog basis: a context assembled as pwqt_assemble_intrinsic; n_out
+   receives its block size.  Errors: as pwqt_assemble_intrinsic; INVALID_ARG for a
+   basis id already present. */
+int pwqt_server_add_basis(pwqt_server* srv, int basis, const pwqt_cell* cell, const pwqt_formfactor* ff,
+                          double gcut, int n_bands, int* n_out);
+
+/* Queue a request; ticket receives its id.  The output buffers must stay valid
+   until pwqt_server_wait has returned PWQT_OK for the ticket.  Errors: INVALID_ARG
+   (unknown basis, sizes, non-finite input), PWQT_ERR_BUSY (queue full),
+   PWQT_ERR_OOM (working set larger than the whole budget). */
+int pwqt_server_submit(pwqt_server* srv, const pwqt_request* req, long long* ticket);
+
+/* Wait up to timeout_s seconds (< 0: without limit) for a request.  PWQT_OK: done,
+   result receives the solve's return code (PWQT_OK or a PWQT_ERR_*, message in
+   pwqt_server_last_error), latency_s the seconds from submission to completion,
+   and the ticket is released.  PWQT_ERR_TIMEOUT: still queued or running (ask
+   again).  PWQT_ERR_INVALID_ARG: unknown or already collected ticket. */
+int pwqt_server_wait(pwqt_server* srv, long long ticket, double timeout_s, int* result, double* latency_s);
+
+/* Completed requests since the last reset, latency percentiles over them (nearest
+   rank), and the largest admitted working-set sum; reset != 0 restarts them. */
+int pwqt_server_stats(pwqt_server* srv, long long* completed, double* p50_s, double* p99_s,
+                      size_t* peak_admitted_bytes, int reset);
+
+/* Message of the last failure on this server (valid until the next failure). */
+const char* pwqt_server_last_error(pwqt_server* srv);
+
+/* Finish the queued requests, stop the workers, release every context.  NULL is
+   accepted. */
+int pwqt_server_destroy(pwqt_server* srv);
 
 /* Launch counters of the library's own kernels since the last reset. */
 int pwqt_kernel_launches(pwqt_ctx* ctx, long long* count, int reset);

@@ -211,11 +211,8 @@ void launch_residual_ff(const ResidualFF& R, const ResJob* jobs, int nb, int m_m
     k_split_solution<<<dim3(256, nb), 256, 0, st>>>(jobs, R.N, R.n, R.Cff, R.per, active);
     const int col_tiles = (std::max(m_max, 1) + CT - 1) / CT;
     const int smem = (int)(sizeof(float4) * (RT * (KC + 1) + KC * CT));
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_residual_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
-    }
+    // idempotent attribute set; per call, so that contexts on several host threads need no shared flag
+    cudaFuncSetAttribute(k_residual_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     k_residual_ff<<<dim3(((R.n + RT - 1) / RT) * col_tiles, R.N, nb), 256, smem, st>>>(R, jobs, col_tiles, active);
     launch_residual_finish(jobs, nb, st, active);
 }

@@ -505,11 +505,8 @@ size_t mixed_bytes_per_energy(int n, int N, int m) {
 
 int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJob>& jobs, SweepJob* jobs_d, std::vector<ResJob>& res,
                 ResJob* res_d, std::vector<ObsJob>& obs, ObsJob* obs_d, int nb, int* iters_dev, cudaStream_t st, bool refine) {
-    static bool inited = false;
-    if (!inited) {
-        if (cgemm_tc_init() != 0) return fail(c, PWQT_ERR_CUDA, "tensor-core GEMM set-up failed");
-        inited = true;
-    }
+    // idempotent (a function attribute of the device): set per call, no flag shared between host threads
+    if (cgemm_tc_init() != 0) return fail(c, PWQT_ERR_CUDA, "tensor-core GEMM set-up failed");
     const int n = sys.n, N = sys.N;
     int m = 0;
     for (int b = 0; b < nb; ++b) m = std::max(m, jobs[b].ms + jobs[b].md);

@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(HERE, "libpwqt.so")
 
 PWQT_OK = 0
 ERR_NAMES = {-1: "INVALID_ARG", -2: "BASIS_TOO_SMALL", -3: "OOM", -4: "CUDA", -5: "STATE", -6: "NO_DEVICE",
-             -7: "TIMEOUT"}
+             -7: "TIMEOUT", -8: "BUSY"}
+ERR_TIMEOUT = -7
 FP64, MIXED, FP32 = 0, 1, 2
 ST_SINGULAR_PIVOT, ST_MODE_COUNT, ST_IR_NO_CONVERGE, ST_DEGENERATE, ST_NEAR_UNIT = 1, 2, 4, 8, 16
 
@@ -25,7 +26,9 @@ EXPORTS = ["pwqt_create", "pwqt_destroy", "pwqt_last_error", "pwqt_assemble_intr
            "pwqt_get_blocks", "pwqt_set_extrinsic", "pwqt_solve", "pwqt_solve_dev", "pwqt_prepare_leads",
            "pwqt_cache_info", "pwqt_bands", "pwqt_kernel_launches", "pwqt_profile", "pwqt_solve_noalloc", "pwqt_cgemm_c64",
            "pwqt_density_reset", "pwqt_accumulate_density", "pwqt_get_density_matrix", "pwqt_density_grid",
-           "pwqt_profile_refinement", "pwqt_set_refinement", "pwqt_solve_multi"]
+           "pwqt_profile_refinement", "pwqt_set_refinement", "pwqt_solve_multi",
+           "pwqt_server_create", "pwqt_server_add_basis", "pwqt_server_submit", "pwqt_server_wait",
+           "pwqt_server_stats", "pwqt_server_last_error", "pwqt_server_destroy"]
 
 
 class PwqtError(RuntimeError):
@@ -37,6 +40,19 @@ class PwqtError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("device", C.c_int), ("hbm_budget_bytes", C.c_size_t), ("ir_tol", C.c_double),
                 ("ir_max_iters", C.c_int), ("batch", C.c_int)]
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("device", C.c_int), ("hbm_budget_bytes", C.c_size_t), ("queue_capacity", C.c_int),
+                ("ir_tol", C.c_double), ("batch", C.c_int)]
+
+
+class RequestC(C.Structure):
+    _fields_ = [("basis", C.c_int), ("n_nodes", C.c_int), ("U", C.POINTER(C.c_double)), ("n_E", C.c_int),
+                ("E", C.POINTER(C.c_double)), ("precision", C.c_int),
+                ("T", C.POINTER(C.c_double)), ("R", C.POINTER(C.c_double)), ("T_ds", C.POINTER(C.c_double)),
+                ("n_open", C.POINTER(C.c_int)), ("node_n", C.POINTER(C.c_double)), ("resid", C.POINTER(C.c_double)),
+                ("iters", C.POINTER(C.c_int)), ("status", C.POINTER(C.c_int))]
 
 
 class CellC(C.Structure):
@@ -81,13 +97,21 @@ def load(path: str = LIB_PATH):
     lib.pwqt_profile_refinement.argtypes = [P, dp, dp, C.POINTER(C.c_longlong)]
     lib.pwqt_set_refinement.argtypes = [P, D, I]
     lib.pwqt_solve_multi.argtypes = [P, I, ip, I, dp, I, dp, dp, dp, ip, dp, dp, ip, ip]
+    lib.pwqt_server_create.argtypes = [C.POINTER(P), C.POINTER(ServerOpts)]
+    lib.pwqt_server_add_basis.argtypes = [P, I, C.POINTER(CellC), C.POINTER(FormFactorC), D, I, ip]
+    lib.pwqt_server_submit.argtypes = [P, C.POINTER(RequestC), C.POINTER(C.c_longlong)]
+    lib.pwqt_server_wait.argtypes = [P, C.c_longlong, D, ip, dp]
+    lib.pwqt_server_stats.argtypes = [P, C.POINTER(C.c_longlong), dp, dp, C.POINTER(S), I]
+    lib.pwqt_server_last_error.argtypes = [P]
+    lib.pwqt_server_last_error.restype = C.c_char_p
+    lib.pwqt_server_destroy.argtypes = [P]
     lib.pwqt_accumulate_density.argtypes = [P, I, I, dp, dp, D, D, D, I, ip]
     lib.pwqt_get_density_matrix.argtypes = [P, I, dp, dp]
     lib.pwqt_density_grid.argtypes = [P, I, I, I, dp]
     fp = C.POINTER(C.c_float)
     lib.pwqt_cgemm_c64.argtypes = [I, I, I, I, fp, I, fp, I, fp, I]
     for f in EXPORTS:
-        if f != "pwqt_last_error":
+        if f not in ("pwqt_last_error", "pwqt_server_last_error"):
             getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -316,3 +340,71 @@ class Context:
         v = C.c_longlong()
         self._check(self.lib.pwqt_kernel_launches(self.h, C.byref(v), 1 if reset else 0))
         return v.value
+
+
+class Server:
+    """pwqt_server: a catalog of bases, requests queued and collected by ticket."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, queue_capacity: int = 0, ir_tol: float = 0.0,
+                 batch: int = 0):
+        self.lib = load()
+        self.h = C.c_void_p()
+        o = ServerOpts(device, hbm_budget_bytes, queue_capacity, ir_tol, batch)
+        r = self.lib.pwqt_server_create(C.byref(self.h), C.byref(o))
+        if r != PWQT_OK:
+            raise PwqtError(r, "pwqt_server_create failed")
+        self.pending = {}
+
+    def _check(self, r):
+        if r != PWQT_OK:
+            raise PwqtError(r, self.lib.pwqt_server_last_error(self.h).decode())
+
+    def add_basis(self, basis: int, cell, ff, gcut: float, n_bands: int) -> int:
+        cc, keep = _cell(cell)
+        f = FormFactorC(ff.v0, ff.sigma)
+        n = C.c_int()
+        self._check(self.lib.pwqt_server_add_basis(self.h, basis, C.byref(cc), C.byref(f), gcut, n_bands, C.byref(n)))
+        return n.value
+
+    def submit(self, basis: int, U, E, precision: int = FP64) -> int:
+        """Queue a request; returns its ticket.  Outputs are held until collected."""
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        nE, N = len(E), len(U)
+        out = SolveResult(np.zeros(nE), np.zeros(nE), np.zeros(nE), np.zeros((nE, 2), np.int32), np.zeros((nE, N, 2)),
+                          np.zeros(nE), np.zeros(nE, np.int32), np.zeros(nE, np.int32))
+        req = RequestC(basis, N, _dptr(U), nE, _dptr(E), precision, _dptr(out.T), _dptr(out.R), _dptr(out.T_ds),
+                       _iptr(out.n_open), _dptr(out.node_n), _dptr(out.resid), _iptr(out.iters), _iptr(out.status))
+        t = C.c_longlong()
+        self._check(self.lib.pwqt_server_submit(self.h, C.byref(req), C.byref(t)))
+        self.pending[t.value] = (out, U, E)   # keep the buffers alive until collected
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = -1.0):
+        """(SolveResult, latency seconds); raises PwqtError on a failed request or timeout."""
+        rc, lat = C.c_int(), C.c_double()
+        r = self.lib.pwqt_server_wait(self.h, ticket, timeout_s, C.byref(rc), C.byref(lat))
+        if r != PWQT_OK:
+            raise PwqtError(r, self.lib.pwqt_server_last_error(self.h).decode())
+        out = self.pending.pop(ticket)[0]
+        if rc.value != PWQT_OK:
+            raise PwqtError(rc.value, self.lib.pwqt_server_last_error(self.h).decode())
+        return out, lat.value
+
+    def stats(self, reset: bool = False):
+        done, p50, p99, peak = C.c_longlong(), C.c_double(), C.c_double(), C.c_size_t()
+        self._check(self.lib.pwqt_server_stats(self.h, C.byref(done), C.byref(p50), C.byref(p99), C.byref(peak),
+                                               1 if reset else 0))
+        return dict(completed=done.value, p50_s=p50.value, p99_s=p99.value, peak_admitted_bytes=peak.value)
+
+    def close(self):
+        if self.h:
+            self.lib.pwqt_server_destroy(self.h)
+            self.h = C.c_void_p()
+            self.pending.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

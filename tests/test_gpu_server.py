@@ -1,0 +1,109 @@
+"""Serving loop (pwqt_server_*) on the GPU: requests on two catalog bases, several
+potentials (more than the 8 kept per basis, so assembled potentials are evicted
+and rebuilt), all three precisions, submitted from two host threads at once.
+Every result must equal the same solve run alone on a separate context (FP64:
+1e-10 relative, the reductions' summation order aside; mixed: the 1e-8 bar of the
+refinement; complex64 alone: its own 1e-3 residual level)."""
+import threading
+
+import numpy as np
+import pytest
+
+from paper_1903_00548_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-10, 1: 1e-8, 2: 1e-3}
+
+
+@pytest.fixture(scope="module")
+def pw():
+    from paper_1903_00548_gb300 import build, pwqt
+    build.build()
+    return pwqt
+
+
+def _catalog():
+    chain = W.chain8()
+    rib_cell = W.armchair_ribbon_cell(W.ribbon_lines_for_width(0.5))
+    return {0: (chain.cell, chain.ff, chain.gcut, chain.n_bands), 1: (rib_cell, W.FormFactor(), 28.0, 12)}
+
+
+def _requests():
+    rng = np.random.default_rng(7)
+    reqs = []
+    for q in range(20):
+        basis = q % 2
+        N = 12 + 4 * (q % 3)
+        pot = (q // 2) % 10                       # ten potentials per basis
+        U = W.random_smooth(N, 0.2, 100 + pot)
+        nE = 3 + q % 4
+        E = np.sort(rng.uniform(0.2, 1.4, nE))
+        reqs.append((basis, U, E, [0, 1, 2][q % 3]))
+    return reqs
+
+
+def test_server_results_equal_standalone_solves(pw):
+    cat = _catalog()
+    srv = pw.Server()
+    ns = {b: srv.add_basis(b, *cat[b]) for b in cat}
+    assert ns[0] == 8 and ns[1] == 24
+    reqs = _requests()
+    tickets = [None] * len(reqs)
+
+    def submitter(idx):
+        for k in idx:
+            b, U, E, p = reqs[k]
+            tickets[k] = srv.submit(b, U, E, p)
+
+    th = [threading.Thread(target=submitter, args=(list(range(s, len(reqs), 2)),)) for s in (0, 1)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    results = [srv.wait(t) for t in tickets]
+    st = srv.stats()
+    assert st["completed"] == len(reqs)
+    assert 0 < st["p50_s"] <= st["p99_s"]
+    assert st["peak_admitted_bytes"] > 0
+    # the same solves, one by one, on separate contexts
+    refs = {}
+    for b in cat:
+        ctx = pw.Context()
+        ctx.assemble_intrinsic(*cat[b])
+        refs[b] = ctx
+    for k, (b, U, E, p) in enumerate(reqs):
+        ctx = refs[b]
+        ctx.set_extrinsic(0, U)
+        ref = ctx.solve(0, E, p)
+        got, lat = results[k]
+        assert lat > 0
+        assert np.array_equal(got.n_open, ref.n_open), k
+        scale = np.maximum(1.0, np.abs(ref.T))
+        assert np.all(np.abs(got.T - ref.T) <= TOL[p] * scale), (k, p, got.T, ref.T)
+        assert np.all(np.abs(got.R - ref.R) <= TOL[p] * scale), (k, p)
+        if p == 0:
+            nn = np.max(np.abs(ref.node_n))
+            assert np.max(np.abs(got.node_n - ref.node_n)) <= 1e-10 * nn, k
+            assert np.all(got.status == ref.status), k
+    srv.close()
+
+
+def test_server_errors(pw):
+    cat = _catalog()
+    srv = pw.Server(hbm_budget_bytes=1 << 30)
+    srv.add_basis(0, *cat[0])
+    with pytest.raises(pw.PwqtError):
+        srv.add_basis(0, *cat[0])                          # id taken
+    with pytest.raises(pw.PwqtError):
+        srv.submit(3, np.zeros(10), np.array([0.5]))       # unknown basis
+    with pytest.raises(pw.PwqtError):
+        srv.submit(0, np.zeros(1), np.array([0.5]))        # one node
+    with pytest.raises(pw.PwqtError):
+        srv.submit(0, np.zeros(10), np.array([np.nan]))
+    t = srv.submit(0, np.zeros(10), np.array([0.5, 0.9]))
+    res, _ = srv.wait(t)
+    assert np.all(np.abs(res.T - np.round(res.T)) < 1e-8)   # pristine chain: integer plateaus
+    with pytest.raises(pw.PwqtError):
+        srv.wait(t)                                        # collected already
+    srv.close()
