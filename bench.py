@@ -38,9 +38,9 @@ L2_BYTES = 129 * 2 ** 20
 # nominal dense rates of GB300 used to scale the measured bf16 peak to other dtypes
 NOMINAL_TFLOPS = {"bf16": 2250.0, "tf32": 1100.0, "f64": 1.25}
 # FP32 instructions per complex multiply-add of the float-float residual: four
-# float-float multiply-adds of 11 instructions (product, its FMA error, two cross
-# terms, two-sum of the leading parts, low-part update)
-FF_INST_PER_CMAC = 44
+# float-float multiply-adds of 12 instructions each (product, its FMA error, two
+# cross terms, five for the two-sum of the leading parts, two for the low part)
+FF_INST_PER_CMAC = 48
 # DRAM bytes (read + write) of one k_residual_ff launch per (node, energy) at block 512 and
 # ~91 injected modes, from the ncu capture summarised in
 # profiles/k_residual_ff_ribbon512_n20_b8.md (1.807 GB for 20 nodes x 8 energies); the
@@ -428,14 +428,14 @@ def run_serving(args, world, rank, local):
     if rank != 0:
         return 0
     torch.cuda.set_device(local)
-    rib15 = W.armchair_ribbon_cell(W.ribbon_lines_for_width(1.5))
+    # one structure (the 13 nm ribbon, whose Bloch basis stays well conditioned) at four
+    # block sizes; energy windows inside each basis' band range (top Gamma/Z bands:
+    # 1.0/1.4 eV at 32 bands, 7.0/3.1 eV at 64, 8.9/9.5 eV at 128)
     wl512 = W.ribbon512()
-    cat = {64: (rib15, W.FormFactor(), 45.0, 32), 128: (rib15, W.FormFactor(), 45.0, 64),
-           256: (rib15, W.FormFactor(), 45.0, 128), 512: (wl512.cell, wl512.ff, wl512.gcut, wl512.n_bands)}
-    # windows inside each basis' band range (its top band: ~10.6 eV at n = 64, ~21 eV at n = 128)
-    grids = {64: np.linspace(3.0, 4.0, 48), 128: np.linspace(10.0, 11.0, 48),
-             256: np.linspace(W.RIBBON15_G45_ECB - 0.05, W.RIBBON15_G45_ECB + 0.8, 48),
-             512: np.linspace(W.RIBBON13_G30_E64 - 0.05, W.RIBBON13_G30_E64 + 0.9, 48)}
+    cat = {2 * b: (wl512.cell, wl512.ff, wl512.gcut, b) for b in (32, 64, 128, 256)}
+    e64 = W.RIBBON13_G30_E64
+    grids = {64: np.linspace(0.0, 0.9, 48), 128: np.linspace(1.5, 2.8, 48),
+             256: np.linspace(e64 - 0.05, e64 + 0.9, 48), 512: np.linspace(e64 - 0.05, e64 + 0.9, 48)}
     srv = pw.Server(device=local)
     t0 = time.perf_counter()
     for nb in cat:
@@ -499,7 +499,8 @@ def run_serving(args, world, rank, local):
             "latency_s": {"p50": st["p50_s"], "p99": st["p99_s"]}, "capacity_solves_per_s": cap,
             "arrival_rate_req_per_s": 0.7 * req_rate, "requests": n_req, "bad_status": bad, "setup_s": t_setup,
             "data": "synthetic",
-            "config": {"workload": "serving", "catalog_block_sizes": sorted(cat), "nodes": "U[50,200]",
+            "config": {"workload": "serving", "structure": "13 nm armchair ribbon, G_cut 30 nm^-1",
+                       "catalog_block_sizes": sorted(cat), "nodes": "U[50,200]",
                        "energies_per_request": "log-uniform 4..32 from a 48-point grid per basis",
                        "precision_mix": "50% complex64 alone (PWQT_FP32), 50% mixed + refinement",
                        "arrivals": "Poisson at 70% of the measured closed-loop request rate, seed 7"}}

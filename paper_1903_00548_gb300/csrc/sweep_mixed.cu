@@ -548,8 +548,10 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         return fail(c, PWQT_ERR_INVALID_ARG, "the complex64 panel of block size " + std::to_string(n) +
                                                  " exceeds shared memory: use PWQT_FP64 (mixed precision takes n <= " +
                                                  std::to_string(smem_optin / (int)(sizeof(float2) * PW) - 1) + ")");
-    if (panel_smem > 48 * 1024)
-        PWQT_CUDA(c, cudaFuncSetAttribute(k_mx_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem));
+    // the limit is a property of the kernel, shared by every context in the process (several
+    // contexts on several host threads run here at once): always the device maximum, never a
+    // per-call value that another thread could lower under a launch in flight
+    PWQT_CUDA(c, cudaFuncSetAttribute(k_mx_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
     auto gemm = [&](const float2* A, long long sA, int lda, const float2* B1, long long sB1, int ldb1, const float2* B2, long long sB2,
                     int ldb2, float2* C1, long long sC1, int ldc1, float2* C2, long long sC2, int ldc2, int split, int M, int Nc, int K) {
         CGemmArgs g{A, sA, lda, B1, sB1, ldb1, B2, sB2, ldb2, C1, sC1, ldc1, C2, sC2, ldc2, split};
@@ -614,8 +616,8 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
     }
     PWQT_CUDA(c, cudaMemcpyAsync(res_d, res.data(), sizeof(ResJob) * nb, cudaMemcpyHostToDevice, st));
     const size_t lus_smem = lusolve_smem(n);
-    if (lus_smem > 48 * 1024)
-        PWQT_CUDA(c, cudaFuncSetAttribute(k_mx_lusolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lus_smem));
+    if (lus_smem > (size_t)smem_optin) return fail(c, PWQT_ERR_INVALID_ARG, "correction solve exceeds shared memory");
+    PWQT_CUDA(c, cudaFuncSetAttribute(k_mx_lusolve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
     std::vector<double> resid(nb, 1.0), prev(nb, 1e300);
     std::vector<int> iters(nb, 0), active(nb, 1), stall(nb, 0), bits(nb, 0);
     const double tol = c->opts.ir_tol;

@@ -26,7 +26,11 @@ def pw():
 def _catalog():
     chain = W.chain8()
     rib_cell = W.armchair_ribbon_cell(W.ribbon_lines_for_width(0.5))
-    return {0: (chain.cell, chain.ff, chain.gcut, chain.n_bands), 1: (rib_cell, W.FormFactor(), 28.0, 12)}
+    wl = W.ribbon512()
+    # basis 2 (block 256) needs more than 48 KB of shared memory per CTA in its panel and
+    # correction kernels: contexts of different block sizes share those kernels' limits
+    return {0: (chain.cell, chain.ff, chain.gcut, chain.n_bands), 1: (rib_cell, W.FormFactor(), 28.0, 12),
+            2: (wl.cell, wl.ff, wl.gcut, 128)}
 
 
 def _requests():
@@ -40,6 +44,10 @@ def _requests():
         nE = 3 + q % 4
         E = np.sort(rng.uniform(0.2, 1.4, nE))
         reqs.append((basis, U, E, [0, 1, 2][q % 3]))
+    e64 = W.RIBBON13_G30_E64
+    for q in range(4):
+        U = W.random_smooth(10, 0.2, 300 + q % 2)
+        reqs.append((2, U, np.array([e64 + 0.1 + 0.2 * q, e64 + 0.35 + 0.2 * q]), [1, 0][q % 2]))
     return reqs
 
 
@@ -47,7 +55,7 @@ def test_server_results_equal_standalone_solves(pw):
     cat = _catalog()
     srv = pw.Server()
     ns = {b: srv.add_basis(b, *cat[b]) for b in cat}
-    assert ns[0] == 8 and ns[1] == 24
+    assert ns[0] == 8 and ns[1] == 24 and ns[2] == 256
     reqs = _requests()
     tickets = [None] * len(reqs)
 
