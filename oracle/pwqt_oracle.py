@@ -717,3 +717,84 @@ def density_from_matrix(basis: BlochBasis, rd, ru, nx, nz):
         t_lr = np.einsum("pa,ab,pb->p", Phi.conj(), ru[e], Phr)
         dens[e] = (fl * fl * t_ll + fr * fr * t_rr + 2.0 * fl * fr * t_lr).real
     return dens.reshape(N - 1, nxe, nz)
+
+
+# =============================================================================
+# Sec. 3.3 (density integral) and Eq. current -- adaptive Simpson integration
+# =============================================================================
+
+# 2e^2/h in A/V: with energies in eV, I [A] = G0 * integral of (T_sd f_s - T_ds f_d) dE [eV]
+G0_SIEMENS = 2.0 * 1.602176634e-19 ** 2 / 6.62607015e-34
+
+
+def adaptive_simpson(f, a, b, tol, min_pieces=8, max_evals=4000):
+    """Adaptive Simpson quadrature of a (vector-valued) f over [a, b] (Sec. 3.3: the
+    energy integrals are evaluated adaptively to a prescribed tolerance).
+
+    [a, b] starts as min_pieces equal intervals.  An interval of length h with
+    midpoint m and quarter points l, r is accepted when the one- and two-panel
+    Simpson estimates S1 = h/6 (f_a + 4 f_m + f_b) and S2 = h/12 (f_a + 4 f_l +
+    2 f_m + 4 f_r + f_b) differ by at most 15 tol h / (b - a) in the max norm over
+    the components; it then contributes S2 + (S2 - S1)/15 (Richardson), otherwise
+    each half is treated the same way.  When max_evals evaluations have been spent,
+    the intervals still open are accepted as they stand.
+    Returns (integral, error estimate sum |S2 - S1| / 15, sorted energies used,
+    their quadrature weights)."""
+    cache = {}
+
+    def F(x):
+        if x not in cache:
+            cache[x] = np.atleast_1d(np.asarray(f(x), dtype=float))
+        return cache[x]
+
+    total = np.zeros_like(F(a))
+    err = 0.0
+    weights = {}
+    L = b - a
+
+    def accept(x0, x1, S1, S2):
+        nonlocal total, err
+        total = total + S2 + (S2 - S1) / 15.0
+        err += float(np.max(np.abs(S2 - S1))) / 15.0
+        h = x1 - x0
+        for x, w in zip((x0, x0 + h / 4, x0 + h / 2, x0 + 3 * h / 4, x1), (7, 32, 12, 32, 7)):
+            weights[x] = weights.get(x, 0.0) + w * h / 90.0
+
+    def piece(x0, x1):
+        # depth first, left half before right half (an explicit stack instead of recursion)
+        stack = [(x0, x1)]
+        while stack:
+            x0, x1 = stack.pop()
+            h = x1 - x0
+            xm = x0 + h / 2
+            fa, fm, fb = F(x0), F(xm), F(x1)
+            fl, fr = F(x0 + h / 4), F(x0 + 3 * h / 4)
+            S1 = h / 6.0 * (fa + 4 * fm + fb)
+            S2 = h / 12.0 * (fa + 4 * fl + 2 * fm + 4 * fr + fb)
+            if np.max(np.abs(S2 - S1)) <= 15.0 * tol * h / L or len(cache) >= max_evals or h <= L * 2.0 ** -40:
+                accept(x0, x1, S1, S2)
+            else:
+                stack.append((xm, x1))
+                stack.append((x0, xm))
+
+    edges = a + (b - a) * np.arange(min_pieces + 1) / min_pieces
+    for k in range(min_pieces):
+        piece(float(edges[k]), float(edges[k + 1]))
+    xs = np.array(sorted(weights))
+    return total, err, xs, np.array([weights[x] for x in xs])
+
+
+def current_integrand(sys_, mu_s, mu_d, kT, cache=None):
+    """Eq. current (reading): G0 (T_sd(E) f(E - mu_s) - T_ds(E) f(E - mu_d)), in A/eV."""
+    def f(E):
+        r = solve_energy(sys_.blk, sys_.Vd, sys_.Vu, sys_.U, float(E), cache=cache)
+        return G0_SIEMENS * (r.T * fermi(E - mu_s, kT) - r.T_ds * fermi(E - mu_d, kT))
+    return f
+
+
+def node_density_integrand(sys_, mu_s, mu_d, kT, cache=None):
+    """Node density per energy (Sec. 3.3): n^s[i] f(E - mu_s) + n^d[i] f(E - mu_d)."""
+    def f(E):
+        r = solve_energy(sys_.blk, sys_.Vd, sys_.Vu, sys_.U, float(E), cache=cache)
+        return r.node_n[:, 0] * fermi(E - mu_s, kT) + r.node_n[:, 1] * fermi(E - mu_d, kT)
+    return f
