@@ -317,6 +317,38 @@ int pwqt_get_density_matrix(pwqt_ctx* ctx, int sys, double* rho_d, double* rho_u
 int pwqt_density_grid(pwqt_ctx* ctx, int sys, int nx, int nz, double* n_r);
 
 /*
+ * Energy integrals by adaptive Simpson quadrature (Sec. 3.3: the density integral
+ * is evaluated adaptively to a tolerance, with the error estimated on the node
+ * density; Eq. current: the ballistic current with the same method).  Integrands:
+ *   PWQT_INTEGRAND_CURRENT: (2e^2/h) (T_sd(E) f(E - mu_s) - T_ds(E) f(E - mu_d)), so
+ *       that result[0] is the source-to-drain current in A for energies in eV (the
+ *       Landauer form of Eq. current);
+ *   PWQT_INTEGRAND_NODE_DENSITY: n^s[i](E) f(E - mu_s) + n^d[i](E) f(E - mu_d) per
+ *       node (the node densities of pwqt_solve), result[N].
+ * f(x) = 1/(1 + e^{x/kT}) (a step for kT = 0).  [E_lo, E_hi] starts as min_pieces
+ * equal intervals; an interval of length h is accepted when its one- and two-panel
+ * Simpson estimates S1, S2 differ by at most 15 tol h / (E_hi - E_lo) (max norm over
+ * the components) and contributes S2 + (S2 - S1)/15; otherwise both halves are
+ * examined.  Each refinement round solves all the energies it needs in one batched
+ * pwqt_solve with `precision`.  After max_evals solved energies (or at intervals
+ * 2^-40 of the range) open intervals are accepted as they stand.
+ *   err_est  : sum over intervals of max|S2 - S1| / 15 (may be NULL)
+ *   n_evals  : energies solved (may be NULL)
+ *   energies, weights (may be NULL): the quadrature points, ascending, and their
+ *       weights (the integral of any other per-energy quantity is sum w g(E), e.g.
+ *       pwqt_accumulate_density with these weights); at most max_points are written,
+ *       n_points receives the full count.
+ * Errors: PWQT_ERR_STATE (unknown system), PWQT_ERR_INVALID_ARG, and those of
+ * pwqt_solve.
+ */
+#define PWQT_INTEGRAND_CURRENT       0
+#define PWQT_INTEGRAND_NODE_DENSITY  1
+int pwqt_integrate(pwqt_ctx* ctx, int sys, int integrand, double E_lo, double E_hi, double mu_s, double mu_d,
+                   double kT, double tol, int min_pieces, int max_evals, int precision, double* result,
+                   double* err_est, int* n_evals, double* energies, double* weights, int* n_points,
+                   int max_points);
+
+/*
  * Serving loop (continuous admission of solve requests).  A server owns one
  * context per catalog basis, each with its own CUDA stream and host worker thread:
  * requests on different bases run on the device at the same time, requests on one

@@ -19,6 +19,7 @@ PWQT_OK = 0
 ERR_NAMES = {-1: "INVALID_ARG", -2: "BASIS_TOO_SMALL", -3: "OOM", -4: "CUDA", -5: "STATE", -6: "NO_DEVICE",
              -7: "TIMEOUT", -8: "BUSY"}
 ERR_TIMEOUT = -7
+INTEGRAND_CURRENT, INTEGRAND_NODE_DENSITY = 0, 1
 FP64, MIXED, FP32 = 0, 1, 2
 ST_SINGULAR_PIVOT, ST_MODE_COUNT, ST_IR_NO_CONVERGE, ST_DEGENERATE, ST_NEAR_UNIT = 1, 2, 4, 8, 16
 
@@ -28,7 +29,7 @@ EXPORTS = ["pwqt_create", "pwqt_destroy", "pwqt_last_error", "pwqt_assemble_intr
            "pwqt_density_reset", "pwqt_accumulate_density", "pwqt_get_density_matrix", "pwqt_density_grid",
            "pwqt_profile_refinement", "pwqt_set_refinement", "pwqt_solve_multi",
            "pwqt_server_create", "pwqt_server_add_basis", "pwqt_server_submit", "pwqt_server_wait",
-           "pwqt_server_stats", "pwqt_server_last_error", "pwqt_server_destroy"]
+           "pwqt_server_stats", "pwqt_server_last_error", "pwqt_server_destroy", "pwqt_integrate"]
 
 
 class PwqtError(RuntimeError):
@@ -105,6 +106,7 @@ def load(path: str = LIB_PATH):
     lib.pwqt_server_last_error.argtypes = [P]
     lib.pwqt_server_last_error.restype = C.c_char_p
     lib.pwqt_server_destroy.argtypes = [P]
+    lib.pwqt_integrate.argtypes = [P, I, I, D, D, D, D, D, D, I, I, I, dp, dp, ip, dp, dp, ip, I]
     lib.pwqt_accumulate_density.argtypes = [P, I, I, dp, dp, D, D, D, I, ip]
     lib.pwqt_get_density_matrix.argtypes = [P, I, dp, dp]
     lib.pwqt_density_grid.argtypes = [P, I, I, I, dp]
@@ -280,6 +282,21 @@ class Context:
         g = lambda k: C.c_void_p(out.get(k)) if out.get(k) else None
         self._check(self.lib.pwqt_solve_noalloc(self.h, sys, len(E), _dptr(E), g("T"), g("R"), g("T_ds"), g("node_n"),
                                                 g("status"), C.c_void_p(stream_ptr) if stream_ptr else None))
+
+    def integrate(self, sys: int, integrand: int, E_lo: float, E_hi: float, mu_s: float, mu_d: float, kT: float,
+                  tol: float, min_pieces: int = 8, max_evals: int = 4000, precision: int = FP64, max_points: int = 20000):
+        """Adaptive Simpson integral: (result, error estimate, energies solved, quadrature energies, weights)."""
+        dim = 1 if integrand == INTEGRAND_CURRENT else self.n_nodes[sys]
+        res = np.zeros(dim)
+        err = C.c_double()
+        ne, npts = C.c_int(), C.c_int()
+        xs = np.zeros(max_points)
+        ws = np.zeros(max_points)
+        self._check(self.lib.pwqt_integrate(self.h, sys, integrand, E_lo, E_hi, mu_s, mu_d, kT, tol, min_pieces, max_evals,
+                                            precision, _dptr(res), C.byref(err), C.byref(ne), _dptr(xs), _dptr(ws),
+                                            C.byref(npts), max_points))
+        k = min(npts.value, max_points)
+        return res, err.value, ne.value, xs[:k].copy(), ws[:k].copy()
 
     def density_reset(self, sys: int):
         self._check(self.lib.pwqt_density_reset(self.h, sys))
