@@ -798,3 +798,28 @@ def node_density_integrand(sys_, mu_s, mu_d, kT, cache=None):
         r = solve_energy(sys_.blk, sys_.Vd, sys_.Vu, sys_.U, float(E), cache=cache)
         return r.node_n[:, 0] * fermi(E - mu_s, kT) + r.node_n[:, 1] * fermi(E - mu_d, kT)
     return f
+
+
+# =============================================================================
+# Sec. 3.2 (NEGF alternative) -- transmission from the Green's function
+# =============================================================================
+
+def caroli_transmission(blk, Vd, Vu, U, E, cache=None, contacts=None):
+    """T(E) = Tr[Gamma_d G_{N1} Gamma_s G_{N1}^dagger] with G = [E M - H - Sigma]^{-1}
+    (the Green's function of Sec. 3.2) and Gamma_c = i (Sigma_c - Sigma_c^dagger):
+    the source-to-drain transmission without any mode decomposition at the drain.
+    G_{N1} is the last node's block of the solution with the identity injected at
+    the first node."""
+    N, n = Vd.shape[0], blk["n"]
+    cs, cd = contacts if contacts is not None else contacts_at(blk, E, float(U[0]), float(U[-1]), cache)
+    rhs = np.zeros((N * n, n), complex)
+    rhs[:n] = np.eye(n)
+    if N * n <= 4000:
+        G1 = sla.solve(global_matrix(blk, Vd, Vu, E, cs.Sigma, cd.Sigma), rhs)
+    else:
+        ab, (kl, ku) = banded_matrix(blk, Vd, Vu, E, cs.Sigma, cd.Sigma)
+        G1 = sla.solve_banded((kl, ku), ab, rhs)
+    X = G1[(N - 1) * n:]
+    Gs = 1j * (cs.Sigma - cs.Sigma.conj().T)
+    Gd = 1j * (cd.Sigma - cd.Sigma.conj().T)
+    return float(np.trace(Gd @ X @ Gs @ X.conj().T).real)

@@ -181,3 +181,13 @@ def test_pristine_density_is_cell_periodic():
     rd, ru = O.density_matrix(res, np.full(2, 0.1), 5.0, 5.0, 0.025852)
     d = O.density_from_matrix(s.basis, rd, ru, 1, 9)[:, 0, :]
     assert np.max(np.abs(d - d[0][None, :])) < 1e-6 * np.max(d)
+
+
+def test_caroli_transmission_equals_mode_resolved():
+    # the Green's-function form (no mode decomposition at the drain) and the
+    # wave-function form of Eq. transmission are the same number
+    for s, Es in ((chain_system(), (0.3, 0.77, 1.2)), (small_ribbon_system(), (0.6, 1.1))):
+        for E in Es:
+            r = O.solve_energy(s.blk, s.Vd, s.Vu, s.U, E)
+            Tc = O.caroli_transmission(s.blk, s.Vd, s.Vu, s.U, E)
+            assert abs(Tc - r.T) <= 1e-9 * max(1.0, r.T) + 4 * abs(r.T - r.T_ds), (E, Tc, r.T)
