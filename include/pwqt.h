@@ -317,6 +317,17 @@ int pwqt_get_density_matrix(pwqt_ctx* ctx, int sys, double* rho_d, double* rho_u
 int pwqt_density_grid(pwqt_ctx* ctx, int sys, int nx, int nz, double* n_r);
 
 /*
+ * Transmission from the Green's function (Sec. 3.2: G = [E M - H - Sigma]^{-1}, the
+ * NEGF alternative to the wave-function solve): T(E) = Tr[Gamma_d G_{N1} Gamma_s
+ * G_{N1}^H], Gamma_c = i (Sigma_c - Sigma_c^H), with G_{N1} from the FP64 block sweep
+ * with the identity injected at the first node.  Needs no mode decomposition at the
+ * drain: it cross-checks the T of pwqt_solve (the two agree to rounding).  Host
+ * arrays: E, T [n_E]; status [n_E] (may be NULL) receives the PWQT_ST_* bits.
+ * Work per energy ~ the FP64 sweep with n injected columns.  Errors: as pwqt_solve.
+ */
+int pwqt_transmission_caroli(pwqt_ctx* ctx, int sys, int n_E, const double* E, double* T, int* status);
+
+/*
  * Energy integrals by adaptive Simpson quadrature (Sec. 3.3: the density integral
  * is evaluated adaptively to a tolerance, with the error estimated on the node
  * density; Eq. current: the ballistic current with the same method).  Integrands:

@@ -29,7 +29,8 @@ EXPORTS = ["pwqt_create", "pwqt_destroy", "pwqt_last_error", "pwqt_assemble_intr
            "pwqt_density_reset", "pwqt_accumulate_density", "pwqt_get_density_matrix", "pwqt_density_grid",
            "pwqt_profile_refinement", "pwqt_set_refinement", "pwqt_solve_multi",
            "pwqt_server_create", "pwqt_server_add_basis", "pwqt_server_submit", "pwqt_server_wait",
-           "pwqt_server_stats", "pwqt_server_last_error", "pwqt_server_destroy", "pwqt_integrate"]
+           "pwqt_server_stats", "pwqt_server_last_error", "pwqt_server_destroy", "pwqt_integrate",
+           "pwqt_transmission_caroli"]
 
 
 class PwqtError(RuntimeError):
@@ -107,6 +108,7 @@ def load(path: str = LIB_PATH):
     lib.pwqt_server_last_error.restype = C.c_char_p
     lib.pwqt_server_destroy.argtypes = [P]
     lib.pwqt_integrate.argtypes = [P, I, I, D, D, D, D, D, D, I, I, I, dp, dp, ip, dp, dp, ip, I]
+    lib.pwqt_transmission_caroli.argtypes = [P, I, I, dp, dp, ip]
     lib.pwqt_accumulate_density.argtypes = [P, I, I, dp, dp, D, D, D, I, ip]
     lib.pwqt_get_density_matrix.argtypes = [P, I, dp, dp]
     lib.pwqt_density_grid.argtypes = [P, I, I, I, dp]
@@ -297,6 +299,14 @@ class Context:
                                             C.byref(npts), max_points))
         k = min(npts.value, max_points)
         return res, err.value, ne.value, xs[:k].copy(), ws[:k].copy()
+
+    def transmission_caroli(self, sys: int, E):
+        """(T, status) from the Green's function, per energy."""
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        T = np.zeros(len(E))
+        st = np.zeros(len(E), np.int32)
+        self._check(self.lib.pwqt_transmission_caroli(self.h, sys, len(E), _dptr(E), _dptr(T), _iptr(st)))
+        return T, st
 
     def density_reset(self, sys: int):
         self._check(self.lib.pwqt_density_reset(self.h, sys))

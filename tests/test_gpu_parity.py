@@ -296,3 +296,21 @@ def test_fp32_precision_and_multi_system_solve(pw, chain):
     assert np.allclose(multi[1].node_n, r64.node_n, rtol=1e-13, atol=0)
     # pristine system: integer transmission
     assert np.all(np.abs(one.T - np.round(one.T)) < 1e-8)
+
+
+def test_caroli_transmission_cross_check(pw, chain):
+    # Green's-function transmission (FP64 sweep with the identity injected) against the
+    # oracle's Caroli form and the GPU's own mode-resolved T
+    from tests.oracle_fixtures import small_ribbon_system
+    wl, s = chain
+    for sys_, Es in ((s, wl.energies[5:60:9]), (small_ribbon_system(), np.array([0.6, 1.1, 1.7]))):
+        ctx = _ctx_with_basis(pw, sys_)
+        ctx.set_extrinsic(0, sys_.U)
+        Tc, st = ctx.transmission_caroli(0, Es)
+        res = ctx.solve(0, Es, pw.FP64)
+        for e, E in enumerate(Es):
+            ref = O.caroli_transmission(sys_.blk, sys_.Vd, sys_.Vu, sys_.U, float(E))
+            t = 1e-9 * max(1.0, ref) + 4 * abs(res.T[e] - res.T_ds[e])
+            assert abs(Tc[e] - ref) <= t, (E, Tc[e], ref)
+            assert abs(Tc[e] - res.T[e]) <= t, (E, Tc[e], res.T[e])
+        assert np.all(st & pw.ST_MODE_COUNT == 0)
