@@ -823,3 +823,94 @@ def caroli_transmission(blk, Vd, Vu, U, E, cache=None, contacts=None):
     Gs = 1j * (cs.Sigma - cs.Sigma.conj().T)
     Gd = 1j * (cd.Sigma - cd.Sigma.conj().T)
     return float(np.trace(Gd @ X @ Gs @ X.conj().T).real)
+
+
+# =============================================================================
+# Sec. 4 (self-consistent loop): non-linear Poisson by Newton with the semi-classical
+# Jacobian and DIIS, on a 1D finite-element model along z
+# =============================================================================
+
+def dfermi(x, kT):
+    """-d f_FD / dE at E - mu = x."""
+    t = np.tanh(0.5 * x / kT)
+    return 0.25 * (1.0 - t * t) / kT
+
+
+@dataclass
+class Poisson1D:
+    """1D model of Eq. nonlin_poisson_fem on the node hats f_i (the same hats as the
+    basis): (kappa S + gamma M) U = gamma M U_gate + alpha M (n[U] - n_dop), with
+    S_ij = int f_i' f_j' dz, M_ij = int f_i f_j dz; U is the electron potential
+    energy (eV) on the nodes, fixed at both ends by the contacts (Dirichlet),
+    n the node density per nm (Sec. 3.3) integrated over energy with f_FD."""
+    kappa: float                 # stiffness (eV nm)
+    gamma: float                 # coupling to the gate (eV / nm)
+    alpha: float                 # charge coupling (eV nm per unit of n)
+    U_gate: np.ndarray           # (N,) gate potential energy
+    n_dop: np.ndarray            # (N,) fixed background in the units of n
+
+
+def poisson1d_matrices(N, L):
+    S = (np.diag(np.full(N, 2.0)) - np.diag(np.ones(N - 1), 1) - np.diag(np.ones(N - 1), -1)) / L
+    M = (np.diag(np.full(N, 4.0)) + np.diag(np.ones(N - 1), 1) + np.diag(np.ones(N - 1), -1)) * L / 6.0
+    S[0, 0] = S[-1, -1] = 1.0 / L
+    M[0, 0] = M[-1, -1] = L / 3.0
+    return S, M
+
+
+def density_and_jacobian(sys_, mu_s, mu_d, kT, E_lo, E_hi, tol, cache=None, max_evals=4000):
+    """n_i = int [n^s_i f(E - mu_s) + n^d_i f(E - mu_d)] dE / L and the semi-classical
+    Jacobian diagonal d_i = int [n^s_i (-f') + n^d_i (-f')] dE / L (Eq. density_jacobian),
+    both from one adaptive integration of the stacked integrand."""
+    N = sys_.Vd.shape[0]
+    L = sys_.blk["L"]
+
+    def f(E):
+        r = solve_energy(sys_.blk, sys_.Vd, sys_.Vu, sys_.U, float(E), cache=cache)
+        ns, nd = r.node_n[:, 0], r.node_n[:, 1]
+        return np.concatenate([ns * fermi(E - mu_s, kT) + nd * fermi(E - mu_d, kT),
+                               ns * dfermi(E - mu_s, kT) + nd * dfermi(E - mu_d, kT)])
+
+    I, err, xs, w = adaptive_simpson(f, E_lo, E_hi, tol, max_evals=max_evals)
+    return I[:N] / L, I[N:] / L, len(xs)
+
+
+def self_consistent(sys_, model: Poisson1D, mu_s, mu_d, kT, E_lo, E_hi, tol_int, tol_sc=1e-6,
+                    max_iters=60, diis_window=5, cache=None):
+    """Newton-Raphson on F(U) = (kappa S + gamma M) U - gamma M U_gate - alpha M (n[U] - n_dop)
+    (Eq. newton_poisson) over the interior nodes, with the Jacobian kappa S + gamma M +
+    alpha M diag(d) (n decreases where U rises: dn_i/dU_i ~ -d_i, Eq. density_jacobian);
+    the Newton output and its step R = U_new - U enter a DIIS subspace of the last
+    diis_window iterates (Sec. 4: least squares by SVD) whose extrapolation is the next
+    U (diis_window <= 1: plain Newton).  Stops when ||R||_2 <= tol_sc (eV).
+    Returns (U, history of ||R||_2, n, d)."""
+    N = sys_.Vd.shape[0]
+    L = sys_.blk["L"]
+    S, M = poisson1d_matrices(N, L)
+    K = model.kappa * S + model.gamma * M
+    U = np.array(sys_.U, dtype=float)
+    inner = slice(1, N - 1)
+    hist, Us, Rs = [], [], []
+    n = d = None
+    for _ in range(max_iters):
+        s = System(sys_.basis, sys_.elem, sys_.blk, U, *extrinsic_blocks(sys_.blk, U))
+        n, d, _ = density_and_jacobian(s, mu_s, mu_d, kT, E_lo, E_hi, tol_int, cache)
+        F = K @ U - model.gamma * M @ model.U_gate - model.alpha * M @ (n - model.n_dop)
+        J = K + model.alpha * M @ np.diag(d)
+        step = np.zeros(N)
+        step[inner] = -np.linalg.solve(J[inner, inner], F[inner])
+        U_new = U + step
+        hist.append(float(np.linalg.norm(step)))
+        if hist[-1] <= tol_sc:
+            return U_new, hist, n, d
+        if diis_window > 1:
+            Us.append(U_new.copy())
+            Rs.append(step.copy())
+            Us, Rs = Us[-diis_window:], Rs[-diis_window:]
+            if len(Us) > 1:
+                # min || R_m + sum_k c_k (R_k - R_m) ||, coefficients of the older iterates
+                A = np.stack([Rs[k] - Rs[-1] for k in range(len(Rs) - 1)], axis=1)
+                c, *_ = np.linalg.lstsq(A, -Rs[-1], rcond=1e-10)
+                U_new = Us[-1] + sum(c[k] * (Us[k] - Us[-1]) for k in range(len(c)))
+        U = U_new
+    return U, hist, n, d
