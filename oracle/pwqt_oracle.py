@@ -757,7 +757,8 @@ def adaptive_simpson(f, a, b, tol, min_pieces=8, max_evals=4000):
         total = total + S2 + (S2 - S1) / 15.0
         err += float(np.max(np.abs(S2 - S1))) / 15.0
         h = x1 - x0
-        for x, w in zip((x0, x0 + h / 4, x0 + h / 2, x0 + 3 * h / 4, x1), (7, 32, 12, 32, 7)):
+        xm = x0 + (x1 - x0) / 2
+        for x, w in zip((x0, x0 + (xm - x0) / 2, xm, xm + (x1 - xm) / 2, x1), (7, 32, 12, 32, 7)):
             weights[x] = weights.get(x, 0.0) + w * h / 90.0
 
     def piece(x0, x1):
@@ -766,9 +767,12 @@ def adaptive_simpson(f, a, b, tol, min_pieces=8, max_evals=4000):
         while stack:
             x0, x1 = stack.pop()
             h = x1 - x0
-            xm = x0 + h / 2
+            # nested midpoints: a half's own midpoint is computed by the same expression
+            # as this interval's quarter point, so the halves reuse these energies exactly
+            xm = x0 + (x1 - x0) / 2
+            xl, xr = x0 + (xm - x0) / 2, xm + (x1 - xm) / 2
             fa, fm, fb = F(x0), F(xm), F(x1)
-            fl, fr = F(x0 + h / 4), F(x0 + 3 * h / 4)
+            fl, fr = F(xl), F(xr)
             S1 = h / 6.0 * (fa + 4 * fm + fb)
             S2 = h / 12.0 * (fa + 4 * fl + 2 * fm + 4 * fr + fb)
             if np.max(np.abs(S2 - S1)) <= 15.0 * tol * h / L or len(cache) >= max_evals or h <= L * 2.0 ** -40:

@@ -75,10 +75,20 @@ extern "C" int pwqt_integrate(pwqt_ctx* c, int sys, int integrand, double E_lo, 
         open.push_back({E_lo + (E_hi - E_lo) * k / min_pieces, E_lo + (E_hi - E_lo) * (k + 1) / min_pieces});
     while (!open.empty()) {
         std::vector<double> need;
+        // nested midpoints: a half's midpoint is the same expression as this interval's
+        // quarter point, so the halves reuse these energies exactly
+        auto points = [](const Piece& p, double* x) {
+            x[0] = p.x0;
+            x[2] = p.x0 + (p.x1 - p.x0) / 2;
+            x[1] = p.x0 + (x[2] - p.x0) / 2;
+            x[3] = x[2] + (p.x1 - x[2]) / 2;
+            x[4] = p.x1;
+        };
         for (const Piece& p : open) {
-            const double h = p.x1 - p.x0;
-            for (double x : {p.x0, p.x0 + h / 4, p.x0 + h / 2, p.x0 + 3 * h / 4, p.x1})
-                if (!cache.count(x)) need.push_back(x);
+            double x[5];
+            points(p, x);
+            for (double v : x)
+                if (!cache.count(v)) need.push_back(v);
         }
         std::sort(need.begin(), need.end());
         need.erase(std::unique(need.begin(), need.end()), need.end());
@@ -86,9 +96,12 @@ extern "C" int pwqt_integrate(pwqt_ctx* c, int sys, int integrand, double E_lo, 
         const bool spent = (int)cache.size() >= max_evals;
         std::vector<Piece> next;
         for (const Piece& p : open) {
-            const double h = p.x1 - p.x0, xm = p.x0 + h / 2;
-            const std::vector<double>&fa = cache[p.x0], &fl = cache[p.x0 + h / 4], &fm = cache[xm],
-                                       &fr = cache[p.x0 + 3 * h / 4], &fb = cache[p.x1];
+            const double h = p.x1 - p.x0;
+            double xs[5];
+            points(p, xs);
+            const double xm = xs[2];
+            const std::vector<double>&fa = cache[xs[0]], &fl = cache[xs[1]], &fm = cache[xs[2]], &fr = cache[xs[3]],
+                                       &fb = cache[xs[4]];
             double d = 0.0;
             std::vector<double> S1(dim), S2(dim);
             for (int q = 0; q < dim; ++q) {
@@ -99,7 +112,6 @@ extern "C" int pwqt_integrate(pwqt_ctx* c, int sys, int integrand, double E_lo, 
             if (d <= 15.0 * tol * h / L || spent || h <= L * std::ldexp(1.0, -40)) {
                 for (int q = 0; q < dim; ++q) total[q] += S2[q] + (S2[q] - S1[q]) / 15.0;
                 err += d / 15.0;
-                const double xs[5] = {p.x0, p.x0 + h / 4, xm, p.x0 + 3 * h / 4, p.x1};
                 const double ws[5] = {7, 32, 12, 32, 7};
                 for (int k = 0; k < 5; ++k) wmap[xs[k]] += ws[k] * h / 90.0;
             } else {

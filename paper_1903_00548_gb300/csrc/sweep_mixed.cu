@@ -551,7 +551,13 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
     // the limit is a property of the kernel, shared by every context in the process (several
     // contexts on several host threads run here at once): always the device maximum, never a
     // per-call value that another thread could lower under a launch in flight
-    PWQT_CUDA(c, cudaFuncSetAttribute(k_mx_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
+    cudaFuncAttributes fa_panel{}, fa_lus{};
+    PWQT_CUDA(c, cudaFuncGetAttributes(&fa_panel, k_mx_panel));
+    PWQT_CUDA(c, cudaFuncGetAttributes(&fa_lus, k_mx_lusolve));
+    // the opt-in maximum counts static and dynamic shared memory together
+    const int dyn_panel = smem_optin - (int)fa_panel.sharedSizeBytes, dyn_lus = smem_optin - (int)fa_lus.sharedSizeBytes;
+    if (panel_smem > (size_t)dyn_panel) return fail(c, PWQT_ERR_INVALID_ARG, "panel exceeds shared memory");
+    PWQT_CUDA(c, cudaFuncSetAttribute(k_mx_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_panel));
     auto gemm = [&](const float2* A, long long sA, int lda, const float2* B1, long long sB1, int ldb1, const float2* B2, long long sB2,
                     int ldb2, float2* C1, long long sC1, int ldc1, float2* C2, long long sC2, int ldc2, int split, int M, int Nc, int K) {
         CGemmArgs g{A, sA, lda, B1, sB1, ldb1, B2, sB2, ldb2, C1, sC1, ldc1, C2, sC2, ldc2, split};
@@ -616,8 +622,8 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
     }
     PWQT_CUDA(c, cudaMemcpyAsync(res_d, res.data(), sizeof(ResJob) * nb, cudaMemcpyHostToDevice, st));
     const size_t lus_smem = lusolve_smem(n);
-    if (lus_smem > (size_t)smem_optin) return fail(c, PWQT_ERR_INVALID_ARG, "correction solve exceeds shared memory");
-    PWQT_CUDA(c, cudaFuncSetAttribute(k_mx_lusolve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
+    if (lus_smem > (size_t)dyn_lus) return fail(c, PWQT_ERR_INVALID_ARG, "correction solve exceeds shared memory");
+    PWQT_CUDA(c, cudaFuncSetAttribute(k_mx_lusolve, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_lus));
     std::vector<double> resid(nb, 1.0), prev(nb, 1e300);
     std::vector<int> iters(nb, 0), active(nb, 1), stall(nb, 0), bits(nb, 0);
     const double tol = c->opts.ir_tol;
