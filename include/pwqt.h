@@ -352,12 +352,48 @@ int pwqt_transmission_caroli(pwqt_ctx* ctx, int sys, int n_E, const double* E, d
  * Errors: PWQT_ERR_STATE (unknown system), PWQT_ERR_INVALID_ARG, and those of
  * pwqt_solve.
  */
-#define PWQT_INTEGRAND_CURRENT       0
-#define PWQT_INTEGRAND_NODE_DENSITY  1
+#define PWQT_INTEGRAND_CURRENT                0
+#define PWQT_INTEGRAND_NODE_DENSITY           1
+#define PWQT_INTEGRAND_NODE_DENSITY_JACOBIAN  2   /* result[2N]: the node density, then the same
+                                                     with -df/dE in place of f (Eq. density_jacobian) */
 int pwqt_integrate(pwqt_ctx* ctx, int sys, int integrand, double E_lo, double E_hi, double mu_s, double mu_d,
                    double kT, double tol, int min_pieces, int max_evals, int precision, double* result,
                    double* err_est, int* n_evals, double* energies, double* weights, int* n_points,
                    int max_points);
+
+/*
+ * Self-consistent potential (Sec. 4) on a 1D finite-element model of the non-linear
+ * Poisson equation (Eq. nonlin_poisson_fem) along z, on the node hats f_i:
+ *     (kappa S + gamma M) U = gamma M U_gate + alpha M (n[U] - n_dop),
+ * S_ij = int f_i' f_j', M_ij = int f_i f_j (tridiagonal, node spacing Lz), U the
+ * electron potential energy (eV) on the N nodes of system `sys`, held at U[0] and
+ * U[N-1] (the contacts), n the node density per nm integrated over [E_lo, E_hi]
+ * with f_FD (pwqt_integrate, tolerance tol_int).  Newton-Raphson (Eq. newton_poisson)
+ * with the semi-classical Jacobian kappa S + gamma M + alpha M diag(d), d the node
+ * density integrated with -df/dE (Eq. density_jacobian); the Newton outputs and
+ * steps of the last diis_window iterates form the DIIS subspace (least squares by
+ * SVD, singular values below 1e-10 of the largest dropped) whose extrapolation is the
+ * next potential (diis_window <= 1: plain Newton).  Stops when the l2 norm of the
+ * Newton step is <= tol_sc (eV).
+ *   U       in: the starting potential (N values, ends fixed); out: the result.
+ *   history (may be NULL, max_iters values): the step norm of every iteration.
+ *   iters   receives the iteration count; n_out (may be NULL): n at the result.
+ * The system's extrinsic blocks are rebuilt every iteration (pwqt_set_extrinsic);
+ * the contact self-energy cache is reused (the contacts do not move).  Returns
+ * PWQT_ERR_STATE if not converged within max_iters (U holds the last iterate).
+ */
+typedef struct {
+    double        kappa;       /* eV nm                                               */
+    double        gamma;       /* eV / nm                                             */
+    double        alpha;       /* eV nm per unit of the node density per nm           */
+    const double* U_gate;      /* N values (eV)                                       */
+    const double* n_dop;       /* N values, in the units of the node density per nm   */
+} pwqt_poisson1d;
+
+int pwqt_self_consistent(pwqt_ctx* ctx, int sys, const pwqt_poisson1d* model, double mu_s, double mu_d,
+                         double kT, double E_lo, double E_hi, double tol_int, double tol_sc, int max_iters,
+                         int diis_window, int precision, double* U, double* history, int* iters,
+                         double* n_out);
 
 /*
  * Serving loop (continuous admission of solve requests).  A server owns one

@@ -28,6 +28,13 @@ double fermi_fd(double x, double kT) {
     return 0.5 * (1.0 - std::tanh(0.5 * x / kT));
 }
 
+// -d f_FD / dE at E - mu = x (zero for kT = 0: the step's derivative is not sampled)
+double dfermi_fd(double x, double kT) {
+    if (kT <= 0) return 0.0;
+    const double t = std::tanh(0.5 * x / kT);
+    return 0.25 * (1.0 - t * t) / kT;
+}
+
 struct Piece { double x0, x1; };
 
 }  // namespace
@@ -39,13 +46,14 @@ extern "C" int pwqt_integrate(pwqt_ctx* c, int sys, int integrand, double E_lo, 
     if (!c) return PWQT_ERR_INVALID_ARG;
     auto it = c->systems.find(sys);
     if (it == c->systems.end()) return fail(c, PWQT_ERR_STATE, "unknown system: call pwqt_set_extrinsic first");
-    if (integrand != PWQT_INTEGRAND_CURRENT && integrand != PWQT_INTEGRAND_NODE_DENSITY)
+    if (integrand != PWQT_INTEGRAND_CURRENT && integrand != PWQT_INTEGRAND_NODE_DENSITY &&
+        integrand != PWQT_INTEGRAND_NODE_DENSITY_JACOBIAN)
         return fail(c, PWQT_ERR_INVALID_ARG, "unknown integrand");
     if (!(E_hi > E_lo) || !std::isfinite(E_lo) || !std::isfinite(E_hi) || !(tol > 0) || !std::isfinite(mu_s) ||
         !std::isfinite(mu_d) || !(kT >= 0) || min_pieces < 1 || max_evals < 1 || !result)
         return fail(c, PWQT_ERR_INVALID_ARG, "need E_lo < E_hi, tol > 0, kT >= 0, min_pieces >= 1, max_evals >= 1, result");
     const int N = it->second.N;
-    const int dim = integrand == PWQT_INTEGRAND_CURRENT ? 1 : N;
+    const int dim = integrand == PWQT_INTEGRAND_CURRENT ? 1 : (integrand == PWQT_INTEGRAND_NODE_DENSITY ? N : 2 * N);
     const double L = E_hi - E_lo;
     std::map<double, std::vector<double>> cache;   // integrand value per solved energy
 
@@ -54,7 +62,7 @@ extern "C" int pwqt_integrate(pwqt_ctx* c, int sys, int integrand, double E_lo, 
         const int nE = (int)xs.size();
         std::vector<double> T(nE), Tds(nE), nn((size_t)nE * N * 2);
         int rc = pwqt_solve(c, sys, nE, xs.data(), precision, T.data(), nullptr, Tds.data(), nullptr,
-                            integrand == PWQT_INTEGRAND_NODE_DENSITY ? nn.data() : nullptr, nullptr, nullptr, nullptr);
+                            integrand != PWQT_INTEGRAND_CURRENT ? nn.data() : nullptr, nullptr, nullptr, nullptr);
         if (rc != PWQT_OK) return rc;
         for (int e = 0; e < nE; ++e) {
             const double fs = fermi_fd(xs[e] - mu_s, kT), fd = fermi_fd(xs[e] - mu_d, kT);
@@ -62,6 +70,10 @@ extern "C" int pwqt_integrate(pwqt_ctx* c, int sys, int integrand, double E_lo, 
             if (integrand == PWQT_INTEGRAND_CURRENT) v[0] = G0_SIEMENS * (T[e] * fs - Tds[e] * fd);
             else
                 for (int i = 0; i < N; ++i) v[i] = nn[((size_t)e * N + i) * 2] * fs + nn[((size_t)e * N + i) * 2 + 1] * fd;
+            if (integrand == PWQT_INTEGRAND_NODE_DENSITY_JACOBIAN) {   // second block: -df/dE weights
+                const double gs = dfermi_fd(xs[e] - mu_s, kT), gd = dfermi_fd(xs[e] - mu_d, kT);
+                for (int i = 0; i < N; ++i) v[N + i] = nn[((size_t)e * N + i) * 2] * gs + nn[((size_t)e * N + i) * 2 + 1] * gd;
+            }
             cache[xs[e]] = std::move(v);
         }
         return PWQT_OK;

@@ -19,7 +19,7 @@ PWQT_OK = 0
 ERR_NAMES = {-1: "INVALID_ARG", -2: "BASIS_TOO_SMALL", -3: "OOM", -4: "CUDA", -5: "STATE", -6: "NO_DEVICE",
              -7: "TIMEOUT", -8: "BUSY"}
 ERR_TIMEOUT = -7
-INTEGRAND_CURRENT, INTEGRAND_NODE_DENSITY = 0, 1
+INTEGRAND_CURRENT, INTEGRAND_NODE_DENSITY, INTEGRAND_NODE_DENSITY_JACOBIAN = 0, 1, 2
 FP64, MIXED, FP32 = 0, 1, 2
 ST_SINGULAR_PIVOT, ST_MODE_COUNT, ST_IR_NO_CONVERGE, ST_DEGENERATE, ST_NEAR_UNIT = 1, 2, 4, 8, 16
 
@@ -30,7 +30,7 @@ EXPORTS = ["pwqt_create", "pwqt_destroy", "pwqt_last_error", "pwqt_assemble_intr
            "pwqt_profile_refinement", "pwqt_set_refinement", "pwqt_solve_multi",
            "pwqt_server_create", "pwqt_server_add_basis", "pwqt_server_submit", "pwqt_server_wait",
            "pwqt_server_stats", "pwqt_server_last_error", "pwqt_server_destroy", "pwqt_integrate",
-           "pwqt_transmission_caroli"]
+           "pwqt_transmission_caroli", "pwqt_self_consistent"]
 
 
 class PwqtError(RuntimeError):
@@ -55,6 +55,11 @@ class RequestC(C.Structure):
                 ("T", C.POINTER(C.c_double)), ("R", C.POINTER(C.c_double)), ("T_ds", C.POINTER(C.c_double)),
                 ("n_open", C.POINTER(C.c_int)), ("node_n", C.POINTER(C.c_double)), ("resid", C.POINTER(C.c_double)),
                 ("iters", C.POINTER(C.c_int)), ("status", C.POINTER(C.c_int))]
+
+
+class Poisson1DC(C.Structure):
+    _fields_ = [("kappa", C.c_double), ("gamma", C.c_double), ("alpha", C.c_double),
+                ("U_gate", C.POINTER(C.c_double)), ("n_dop", C.POINTER(C.c_double))]
 
 
 class CellC(C.Structure):
@@ -109,6 +114,7 @@ def load(path: str = LIB_PATH):
     lib.pwqt_server_destroy.argtypes = [P]
     lib.pwqt_integrate.argtypes = [P, I, I, D, D, D, D, D, D, I, I, I, dp, dp, ip, dp, dp, ip, I]
     lib.pwqt_transmission_caroli.argtypes = [P, I, I, dp, dp, ip]
+    lib.pwqt_self_consistent.argtypes = [P, I, C.POINTER(Poisson1DC), D, D, D, D, D, D, D, I, I, I, dp, dp, ip, dp]
     lib.pwqt_accumulate_density.argtypes = [P, I, I, dp, dp, D, D, D, I, ip]
     lib.pwqt_get_density_matrix.argtypes = [P, I, dp, dp]
     lib.pwqt_density_grid.argtypes = [P, I, I, I, dp]
@@ -288,7 +294,7 @@ class Context:
     def integrate(self, sys: int, integrand: int, E_lo: float, E_hi: float, mu_s: float, mu_d: float, kT: float,
                   tol: float, min_pieces: int = 8, max_evals: int = 4000, precision: int = FP64, max_points: int = 20000):
         """Adaptive Simpson integral: (result, error estimate, energies solved, quadrature energies, weights)."""
-        dim = 1 if integrand == INTEGRAND_CURRENT else self.n_nodes[sys]
+        dim = {INTEGRAND_CURRENT: 1, INTEGRAND_NODE_DENSITY: self.n_nodes[sys]}.get(integrand, 2 * self.n_nodes[sys])
         res = np.zeros(dim)
         err = C.c_double()
         ne, npts = C.c_int(), C.c_int()
@@ -299,6 +305,23 @@ class Context:
                                             C.byref(npts), max_points))
         k = min(npts.value, max_points)
         return res, err.value, ne.value, xs[:k].copy(), ws[:k].copy()
+
+    def self_consistent(self, sys: int, U0, kappa: float, gamma: float, alpha: float, U_gate, n_dop, mu_s: float,
+                        mu_d: float, kT: float, E_lo: float, E_hi: float, tol_int: float, tol_sc: float = 1e-6,
+                        max_iters: int = 60, diis_window: int = 5, precision: int = FP64):
+        """(U, history of Newton-step norms, n) of the self-consistent loop; raises if not converged."""
+        U = np.ascontiguousarray(U0, dtype=np.float64).copy()
+        Ug = np.ascontiguousarray(U_gate, dtype=np.float64)
+        nd = np.ascontiguousarray(n_dop, dtype=np.float64)
+        model = Poisson1DC(kappa, gamma, alpha, _dptr(Ug), _dptr(nd))
+        hist = np.zeros(max_iters)
+        it = C.c_int()
+        n = np.zeros(len(U))
+        self._check(self.lib.pwqt_self_consistent(self.h, sys, C.byref(model), mu_s, mu_d, kT, E_lo, E_hi, tol_int, tol_sc,
+                                                  max_iters, diis_window, precision, _dptr(U), _dptr(hist), C.byref(it),
+                                                  _dptr(n)))
+        self.n_nodes[sys] = len(U)
+        return U, hist[:it.value].copy(), n
 
     def transmission_caroli(self, sys: int, E):
         """(T, status) from the Green's function, per energy."""
