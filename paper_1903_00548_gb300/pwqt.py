@@ -294,7 +294,8 @@ class Context:
     def integrate(self, sys: int, integrand: int, E_lo: float, E_hi: float, mu_s: float, mu_d: float, kT: float,
                   tol: float, min_pieces: int = 8, max_evals: int = 4000, precision: int = FP64, max_points: int = 20000):
         """Adaptive Simpson integral: (result, error estimate, energies solved, quadrature energies, weights)."""
-        dim = {INTEGRAND_CURRENT: 1, INTEGRAND_NODE_DENSITY: self.n_nodes[sys]}.get(integrand, 2 * self.n_nodes[sys])
+        N = self.n_nodes.get(sys, 1)   # an unknown system is reported by the library
+        dim = {INTEGRAND_CURRENT: 1, INTEGRAND_NODE_DENSITY: N}.get(integrand, 2 * N)
         res = np.zeros(dim)
         err = C.c_double()
         ne, npts = C.c_int(), C.c_int()
