@@ -328,21 +328,21 @@ int assemble_from_basis(pwqt_ctx* c, const pwqt_cell* cell, int n_bands, const d
     for (int g = 0; g < 2; ++g) {
         size_t rows = n_pw[g];
         std::vector<double2> tmp(rows * nb);
-        PWQT_CUDA(c, cudaMemcpy(tmp.data(), coef_dev + off[g] * nb, sizeof(double2) * rows * nb, cudaMemcpyDeviceToHost));
+        PWQT_CUDA(c, copy_sync(c, tmp.data(), coef_dev + off[g] * nb, sizeof(double2) * rows * nb, cudaMemcpyDeviceToHost));
         hc.assign(rows * nb, make_double2(0, 0));
         for (size_t r = 0; r < rows; ++r)
             for (int b = 0; b < nb; ++b) hc[r * nb + b] = tmp[(size_t)order[g][r] * nb + b];
         PWQT_TRY(alloc(c, Cs[g], sizeof(double2) * rows * nb));
-        PWQT_CUDA(c, cudaMemcpy(Cs[g].p, hc.data(), sizeof(double2) * rows * nb, cudaMemcpyHostToDevice));
+        PWQT_CUDA(c, copy_sync(c, Cs[g].p, hc.data(), sizeof(double2) * rows * nb, cudaMemcpyHostToDevice));
         PWQT_TRY(alloc(c, dmx[g], sizeof(int) * rows));
         PWQT_TRY(alloc(c, dmz[g], sizeof(int) * rows));
-        PWQT_CUDA(c, cudaMemcpy(dmx[g].p, mx[g].data(), sizeof(int) * rows, cudaMemcpyHostToDevice));
-        PWQT_CUDA(c, cudaMemcpy(dmz[g].p, mz[g].data(), sizeof(int) * rows, cudaMemcpyHostToDevice));
+        PWQT_CUDA(c, copy_sync(c, dmx[g].p, mx[g].data(), sizeof(int) * rows, cudaMemcpyHostToDevice));
+        PWQT_CUDA(c, copy_sync(c, dmz[g].p, mz[g].data(), sizeof(int) * rows, cudaMemcpyHostToDevice));
         for (int b = 0; b < 2; ++b) {
             PWQT_TRY(alloc(c, dlo[g][b], sizeof(int) * rows));
             PWQT_TRY(alloc(c, dhi[g][b], sizeof(int) * rows));
-            PWQT_CUDA(c, cudaMemcpy(dlo[g][b].p, lo[g][b].data(), sizeof(int) * rows, cudaMemcpyHostToDevice));
-            PWQT_CUDA(c, cudaMemcpy(dhi[g][b].p, hi[g][b].data(), sizeof(int) * rows, cudaMemcpyHostToDevice));
+            PWQT_CUDA(c, copy_sync(c, dlo[g][b].p, lo[g][b].data(), sizeof(int) * rows, cudaMemcpyHostToDevice));
+            PWQT_CUDA(c, copy_sync(c, dhi[g][b].p, hi[g][b].data(), sizeof(int) * rows, cudaMemcpyHostToDevice));
         }
     }
     PwGroup g0{n_pw[0], dmx[0].as<int>(), dmz[0].as<int>(), Cs[0].as<double2>(), nullptr, nullptr};
@@ -351,7 +351,7 @@ int assemble_from_basis(pwqt_ctx* c, const pwqt_cell* cell, int n_bands, const d
     DBuf sums, d_eps;
     PWQT_TRY(alloc(c, sums, sizeof(double2) * nn * 5));
     PWQT_TRY(alloc(c, d_eps, sizeof(double) * n));
-    PWQT_CUDA(c, cudaMemcpy(d_eps.p, eps_host, sizeof(double) * n, cudaMemcpyHostToDevice));
+    PWQT_CUDA(c, copy_sync(c, d_eps.p, eps_host, sizeof(double) * n, cudaMemcpyHostToDevice));
     double bz = 2.0 * M_PI / cell->Lz;
     dim3 grid((n + 127) / 128, n);
     k_element_sums<<<grid, 128, 0, c->stream>>>(nb, cell->Lz, bz, g0, g1, dlo[0][0].as<int>(), dhi[0][0].as<int>(),
@@ -426,7 +426,7 @@ int build_system_blocks(pwqt_ctx* c, System& s) {
     size_t nn = (size_t)n * n;
     DBuf dU;
     PWQT_TRY(alloc(c, dU, sizeof(double) * N));
-    PWQT_CUDA(c, cudaMemcpy(dU.p, s.U.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+    PWQT_CUDA(c, copy_sync(c, dU.p, s.U.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
     PWQT_TRY(alloc(c, s.HV0, sizeof(double2) * nn * N));
     PWQT_TRY(alloc(c, s.HV1, sizeof(double2) * nn * std::max(N - 1, 1)));
     dim3 grid((unsigned)std::min<size_t>((nn + 255) / 256, 1024), N);

@@ -85,7 +85,7 @@ extern "C" int pwqt_transmission_caroli(pwqt_ctx* c, int sys, int n_E, const dou
     }
     if (c->zero_nn.bytes < sizeof(double2) * nn) {
         PWQT_TRY(alloc(c, c->zero_nn, sizeof(double2) * nn));
-        PWQT_CUDA(c, cudaMemset(c->zero_nn.p, 0, c->zero_nn.bytes));
+        PWQT_CUDA(c, cudaMemsetAsync(c->zero_nn.p, 0, c->zero_nn.bytes, st));
     }
     const double2* zero = c->zero_nn.as<double2>();
     // per energy: the sweep panels N n (2n), one n x n scratch, Gamma_s, Gamma_d, Y, Z

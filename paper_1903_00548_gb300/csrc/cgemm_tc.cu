@@ -246,12 +246,15 @@ void launch_cgemm_tc(const CGemmArgs& args, int nbatch, int M, int N, int K, cud
     k_cgemm_tc<<<grid, THREADS, SMEM_BYTES, st>>>(args, M, N, K);
 }
 
-int cgemm_tc_error(bool reset) {
+int cgemm_tc_error(bool reset, cudaStream_t st) {
+    // read on the stream that ran the GEMMs, after them (the flag is shared by all launches)
     int v = 0;
-    cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int));
+    cudaMemcpyFromSymbolAsync(&v, g_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
     if (reset && v) {
-        int z = 0;
-        cudaMemcpyToSymbol(g_tc_error, &z, sizeof(int));
+        const int z = 0;
+        cudaMemcpyToSymbolAsync(g_tc_error, &z, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+        cudaStreamSynchronize(st);
     }
     return v;
 }
@@ -279,7 +282,7 @@ extern "C" int pwqt_cgemm_c64(int batch, int M, int N, int K, const float* A, in
         launch_cgemm_tc(g, batch, M, N, K, 0);
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) rc = PWQT_ERR_CUDA;
-        else if (cgemm_tc_error(true)) rc = PWQT_ERR_CUDA;
+        else if (cgemm_tc_error(true, 0)) rc = PWQT_ERR_CUDA;
         else cudaMemcpy(C, dC, sizeof(float2) * sc * batch, cudaMemcpyDeviceToHost);
     }
     cudaFree(dA); cudaFree(dB); cudaFree(dC);

@@ -19,6 +19,6 @@ struct CGemmArgs {
 
 int cgemm_tc_init();
 void launch_cgemm_tc(const CGemmArgs& args, int nbatch, int M, int N, int K, cudaStream_t st);
-int cgemm_tc_error(bool reset);
+int cgemm_tc_error(bool reset, cudaStream_t st);
 
 }  // namespace pwqt

@@ -107,7 +107,7 @@ int pwqt_set_enhancement(pwqt_ctx* c, const pwqt_cell* cell, int n_bands, const 
     size_t rows = (size_t)n_pw[0] + n_pw[1];
     DBuf d;
     PWQT_TRY(alloc(c, d, sizeof(double2) * rows * n_bands));
-    PWQT_CUDA(c, cudaMemcpy(d.p, coef, sizeof(double2) * rows * n_bands, cudaMemcpyHostToDevice));
+    PWQT_CUDA(c, copy_sync(c, d.p, coef, sizeof(double2) * rows * n_bands, cudaMemcpyHostToDevice));
     PWQT_TRY(assemble_from_basis(c, cell, n_bands, eps, n_pw, mx, mz, d.as<double2>()));
     if (n_out) *n_out = c->n;
     return PWQT_OK;
@@ -117,11 +117,11 @@ int pwqt_get_blocks(pwqt_ctx* c, double* H0, double* H1, double* M0, double* M1,
     PWQT_TRY(check_ctx(c));
     if (!c->n) return fail(c, PWQT_ERR_STATE, "no basis");
     size_t nn = (size_t)c->n * c->n * sizeof(double2);
-    if (H0) PWQT_CUDA(c, cudaMemcpy(H0, c->H0.p, nn, cudaMemcpyDeviceToHost));
-    if (H1) PWQT_CUDA(c, cudaMemcpy(H1, c->H1.p, nn, cudaMemcpyDeviceToHost));
-    if (M0) PWQT_CUDA(c, cudaMemcpy(M0, c->M0.p, nn, cudaMemcpyDeviceToHost));
-    if (M1) PWQT_CUDA(c, cudaMemcpy(M1, c->M1.p, nn, cudaMemcpyDeviceToHost));
-    if (W) PWQT_CUDA(c, cudaMemcpy(W, c->W.p, 6 * nn, cudaMemcpyDeviceToHost));
+    if (H0) PWQT_CUDA(c, copy_sync(c, H0, c->H0.p, nn, cudaMemcpyDeviceToHost));
+    if (H1) PWQT_CUDA(c, copy_sync(c, H1, c->H1.p, nn, cudaMemcpyDeviceToHost));
+    if (M0) PWQT_CUDA(c, copy_sync(c, M0, c->M0.p, nn, cudaMemcpyDeviceToHost));
+    if (M1) PWQT_CUDA(c, copy_sync(c, M1, c->M1.p, nn, cudaMemcpyDeviceToHost));
+    if (W) PWQT_CUDA(c, copy_sync(c, W, c->W.p, 6 * nn, cudaMemcpyDeviceToHost));
     return PWQT_OK;
 }
 
@@ -166,14 +166,14 @@ int pwqt_solve(pwqt_ctx* c, int sys, int n_E, const double* E, int precision, do
                dno.as<int>(), dit.as<int>(), dst.as<int>()};
     PWQT_TRY(solve_common(c, sys, n_E, E, precision, o, c->stream));
     PWQT_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (T) PWQT_CUDA(c, cudaMemcpy(T, dT.p, sizeof(double) * n_E, cudaMemcpyDeviceToHost));
-    if (R) PWQT_CUDA(c, cudaMemcpy(R, dR.p, sizeof(double) * n_E, cudaMemcpyDeviceToHost));
-    if (T_ds) PWQT_CUDA(c, cudaMemcpy(T_ds, dTds.p, sizeof(double) * n_E, cudaMemcpyDeviceToHost));
-    if (n_open) PWQT_CUDA(c, cudaMemcpy(n_open, dno.p, sizeof(int) * 2 * n_E, cudaMemcpyDeviceToHost));
-    if (node_n) PWQT_CUDA(c, cudaMemcpy(node_n, dnn.p, sizeof(double) * 2 * n_E * N, cudaMemcpyDeviceToHost));
-    if (resid) PWQT_CUDA(c, cudaMemcpy(resid, dres.p, sizeof(double) * n_E, cudaMemcpyDeviceToHost));
-    if (iters) PWQT_CUDA(c, cudaMemcpy(iters, dit.p, sizeof(int) * n_E, cudaMemcpyDeviceToHost));
-    if (status) PWQT_CUDA(c, cudaMemcpy(status, dst.p, sizeof(int) * n_E, cudaMemcpyDeviceToHost));
+    if (T) PWQT_CUDA(c, copy_sync(c, T, dT.p, sizeof(double) * n_E, cudaMemcpyDeviceToHost));
+    if (R) PWQT_CUDA(c, copy_sync(c, R, dR.p, sizeof(double) * n_E, cudaMemcpyDeviceToHost));
+    if (T_ds) PWQT_CUDA(c, copy_sync(c, T_ds, dTds.p, sizeof(double) * n_E, cudaMemcpyDeviceToHost));
+    if (n_open) PWQT_CUDA(c, copy_sync(c, n_open, dno.p, sizeof(int) * 2 * n_E, cudaMemcpyDeviceToHost));
+    if (node_n) PWQT_CUDA(c, copy_sync(c, node_n, dnn.p, sizeof(double) * 2 * n_E * N, cudaMemcpyDeviceToHost));
+    if (resid) PWQT_CUDA(c, copy_sync(c, resid, dres.p, sizeof(double) * n_E, cudaMemcpyDeviceToHost));
+    if (iters) PWQT_CUDA(c, copy_sync(c, iters, dit.p, sizeof(int) * n_E, cudaMemcpyDeviceToHost));
+    if (status) PWQT_CUDA(c, copy_sync(c, status, dst.p, sizeof(int) * n_E, cudaMemcpyDeviceToHost));
     return PWQT_OK;
 }
 
@@ -323,7 +323,7 @@ int pwqt_accumulate_density(pwqt_ctx* c, int sys, int n_E, const double* E, cons
     DensityAcc d{w, mu_s, mu_d, kT};
     PWQT_TRY(solve_common(c, sys, n_E, E, precision, o, c->stream, &d));
     PWQT_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (status) PWQT_CUDA(c, cudaMemcpy(status, o.status, sizeof(int) * ne, cudaMemcpyDeviceToHost));
+    if (status) PWQT_CUDA(c, copy_sync(c, status, o.status, sizeof(int) * ne, cudaMemcpyDeviceToHost));
     return PWQT_OK;
 }
 
@@ -335,8 +335,8 @@ int pwqt_get_density_matrix(pwqt_ctx* c, int sys, double* rho_d, double* rho_u) 
     if (!s.rho_d.p) return fail(c, PWQT_ERR_STATE, "no density accumulated: call pwqt_accumulate_density first");
     cudaSetDevice(c->dev);
     const size_t nn = (size_t)c->n * c->n;
-    if (rho_d) PWQT_CUDA(c, cudaMemcpy(rho_d, s.rho_d.p, sizeof(double2) * nn * s.N, cudaMemcpyDeviceToHost));
-    if (rho_u && s.N > 1) PWQT_CUDA(c, cudaMemcpy(rho_u, s.rho_u.p, sizeof(double2) * nn * (s.N - 1), cudaMemcpyDeviceToHost));
+    if (rho_d) PWQT_CUDA(c, copy_sync(c, rho_d, s.rho_d.p, sizeof(double2) * nn * s.N, cudaMemcpyDeviceToHost));
+    if (rho_u && s.N > 1) PWQT_CUDA(c, copy_sync(c, rho_u, s.rho_u.p, sizeof(double2) * nn * (s.N - 1), cudaMemcpyDeviceToHost));
     return PWQT_OK;
 }
 
@@ -354,7 +354,7 @@ int pwqt_density_grid(pwqt_ctx* c, int sys, int nx, int nz, double* n_r) {
     DBuf out;
     PWQT_TRY(alloc(c, out, sizeof(double) * count));
     PWQT_TRY(density_grid(c, s, nx, nz, out.as<double>(), c->stream));
-    PWQT_CUDA(c, cudaMemcpy(n_r, out.p, sizeof(double) * count, cudaMemcpyDeviceToHost));
+    PWQT_CUDA(c, copy_sync(c, n_r, out.p, sizeof(double) * count, cudaMemcpyDeviceToHost));
     return PWQT_OK;
 }
 

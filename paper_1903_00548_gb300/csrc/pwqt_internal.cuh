@@ -168,6 +168,15 @@ struct pwqt_ctx {
 };
 
 namespace pwqt {
+// Host <-> device copy ordered on the context's stream and complete on return.  A plain
+// cudaMemcpy runs on the legacy default stream, which is not ordered with the context's
+// non-blocking stream: for a pageable host source it may return before the data reaches
+// the device, and a kernel on the context's stream could then read stale memory.
+inline cudaError_t copy_sync(pwqt_ctx* c, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, c->stream);
+    return e != cudaSuccess ? e : cudaStreamSynchronize(c->stream);
+}
+
 // error helpers
 int fail(pwqt_ctx* c, int code, const std::string& msg);
 int cuda_fail(pwqt_ctx* c, cudaError_t e, const char* what);

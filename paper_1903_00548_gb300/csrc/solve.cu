@@ -199,7 +199,8 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
     // injected modes (their status carries PWQT_ST_MODE_COUNT)
     if (c->zero_nn.bytes < sizeof(double2) * nn) {
         PWQT_TRY(alloc(c, c->zero_nn, sizeof(double2) * nn));
-        PWQT_CUDA(c, cudaMemset(c->zero_nn.p, 0, c->zero_nn.bytes));
+        // on the stream of the work that reads it (a plain cudaMemset is not ordered with it)
+        PWQT_CUDA(c, cudaMemsetAsync(c->zero_nn.p, 0, c->zero_nn.bytes, st));
     }
     const double2* zero = c->zero_nn.as<double2>();
     PWQT_BLAS(c, cublasSetStream(c->blas, st));

@@ -336,22 +336,29 @@ size_t lusolve_smem(int n) {
 __device__ __forceinline__ void lu_offdiag(const float2* __restrict__ F, int n, int kb, int wd, int r_begin, int r_end,
                                            float2* Fs, float2* T) {
     const int t = threadIdx.x;
-    for (int rc = r_begin; rc < r_end; rc += LR) {
+    constexpr int PER = LR * PW / NT;
+    // one CTA per (energy, column group) leaves little to hide memory latency: the loads of
+    // the next chunk are issued into registers before this chunk's arithmetic, so they are
+    // in flight while it runs
+    float2 v[PER];
+    auto load = [&](int rc) {
         const int rows = min(LR, r_end - rc);
-        // one CTA per (energy, column group) leaves little to hide memory latency:
-        // issue all of this thread's loads before any store
-        float2 v[LR * PW / NT];
 #pragma unroll
-        for (int u = 0; u < LR * PW / NT; ++u) {
+        for (int u = 0; u < PER; ++u) {
             const int q = t + u * NT, rr = q / PW, l = q % PW;
             v[u] = (rr < rows && l < wd) ? F[(size_t)(rc + rr) * n + kb + l] : make_float2(0.f, 0.f);
         }
+    };
+    if (r_begin < r_end) load(r_begin);
+    for (int rc = r_begin; rc < r_end; rc += LR) {
+        const int rows = min(LR, r_end - rc);
 #pragma unroll
-        for (int u = 0; u < LR * PW / NT; ++u) {
+        for (int u = 0; u < PER; ++u) {
             const int q = t + u * NT;
             Fs[(q / PW) * (PW + 1) + q % PW] = v[u];
         }
         __syncthreads();
+        if (rc + LR < r_end) load(rc + LR);
         for (int q = t; q < rows * LC; q += NT) {
             const int rr = q / LC, g = q % LC;
             float2 a = T[(rc + rr) * LC + g];
@@ -607,7 +614,7 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         c->prof_flops += (56.0 / 3.0) * (double)N * n * n * (double)n * nb;
     }
     PWQT_CUDA(c, cudaGetLastError());
-    if (cgemm_tc_error(true)) return fail(c, PWQT_ERR_TIMEOUT, "tensor-core GEMM: a bounded mbarrier wait gave up");
+    if (cgemm_tc_error(true, st)) return fail(c, PWQT_ERR_TIMEOUT, "tensor-core GEMM: a bounded mbarrier wait gave up");
     k_mx_to64<<<dim3(256, nb), NT, 0, st>>>(S);
     c->launches++;
 
