@@ -394,7 +394,12 @@ def run_ours(args, world, rank, local):
                                    "note": "CUDA events; profiling serialises the host with each phase"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "results": {"max_resid": float(np.max(resid)), "max_iters": int(np.max(iters)),
-                        "status_nonzero": int(np.count_nonzero(status)), "mean_modes": float(nopen.sum(1).mean()),
+                        "status_nonzero": int(np.count_nonzero(status)),
+                        "status_bits": {name: int(np.count_nonzero(status & bit)) for name, bit in
+                                        (("singular_pivot", 1), ("mode_count", 2), ("ir_no_converge", 4),
+                                         ("degenerate", 8), ("near_unit", 16))},
+                        "max_resid_unflagged": float(np.max(resid[(status & 7) == 0])) if np.any((status & 7) == 0) else None,
+                        "mean_modes": float(nopen.sum(1).mean()),
                         "T_mean": float(np.mean(res.T))}}
     if oracle_proc is not None:
         r = finish_oracle_sample(*oracle_proc)
