@@ -19,8 +19,29 @@
 namespace pwqt {
 
 int fail(pwqt_ctx* c, int code, const std::string& msg) {
-    if (c) c->err = msg;
+    if (c) {
+        std::lock_guard<std::mutex> g(c->err_m);
+        c->err = msg;
+    }
     return code;
+}
+
+int Lane::init(int dev) {
+    if (st) return PWQT_OK;
+    if (cudaSetDevice(dev) != cudaSuccess || cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+        return PWQT_ERR_CUDA;
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return PWQT_ERR_CUDA;
+    return PWQT_OK;
+}
+
+void Lane::destroy() {
+    if (st) cudaStreamSynchronize(st);
+    ws_mixed.release(); ws_jobs.release(); ws_obs.release(); ws_res.release(); ws_norms.release();
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e), e = nullptr;
+    if (st) cudaStreamDestroy(st);
+    st = nullptr;
 }
 int cuda_fail(pwqt_ctx* c, cudaError_t e, const char* what) {
     return fail(c, e == cudaErrorMemoryAllocation ? PWQT_ERR_OOM : PWQT_ERR_CUDA,

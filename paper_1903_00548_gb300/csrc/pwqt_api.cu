@@ -78,6 +78,7 @@ int pwqt_destroy(pwqt_ctx* c) {
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->ev2) cudaEventDestroy(c->ev2);
     if (c->ev3) cudaEventDestroy(c->ev3);
+    for (auto& l : c->lanes) l.destroy();
     delete c;
     return PWQT_OK;
 }

@@ -4,8 +4,10 @@
 #include <cublas_v2.h>
 #include <cusolverDn.h>
 
+#include <atomic>
 #include <cstdint>
 #include <map>
+#include <mutex>
 #include <memory>
 #include <string>
 #include <vector>
@@ -120,6 +122,21 @@ struct DensJob {
 
 }  // namespace pwqt
 
+namespace pwqt {
+// One of the two halves of a mixed-precision batch: its own stream, workspaces, profiling
+// events and counters, so that the halves run on two host threads and the GPU overlaps
+// one half's residual (FP32-issue-bound) with the other's latency-bound sweep/correction.
+struct Lane {
+    cudaStream_t st = nullptr;
+    DBuf ws_mixed, ws_jobs, ws_obs, ws_res, ws_norms;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    double prof_ms = 0, prof_flops = 0, prof_phase_ms[2] = {0, 0};
+    long long prof_launches = 0, prof_ir_iters = 0;
+    int init(int dev);      // stream and events on first use
+    void destroy();
+};
+}  // namespace pwqt
+
 struct pwqt_ctx {
     int dev = 0;
     pwqt_opts opts{};
@@ -128,7 +145,8 @@ struct pwqt_ctx {
     cusolverDnHandle_t sol = nullptr;
     cusolverDnParams_t prm = nullptr;
     std::string err;
-    long long launches = 0;
+    std::mutex err_m;                       // the mixed path may fail on two host threads at once
+    std::atomic<long long> launches{0};
     int sm_count = 0;
     // basis
     int n = 0, n_bands = 0;
@@ -162,8 +180,11 @@ struct pwqt_ctx {
     // host threads that fill the contact cache concurrently
     int lead_threads = 8;
     std::vector<std::unique_ptr<pwqt::LeadWorker>> workers;
+    // the two halves of a mixed-precision batch (lane 0 also serves undivided batches)
+    pwqt::Lane lanes[2];
     ~pwqt_ctx() {
         for (auto& w : workers) w->destroy();
+        for (auto& l : lanes) l.destroy();
     }
 };
 

@@ -3,6 +3,7 @@
 // (node density, Eq. transmission, reflection) -- all in the library's kernels.
 #include <algorithm>
 #include <cmath>
+#include <thread>
 
 #include "pwqt_internal.cuh"
 #include "sweep_common.cuh"
@@ -204,35 +205,29 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
     }
     const double2* zero = c->zero_nn.as<double2>();
     PWQT_BLAS(c, cublasSetStream(c->blas, st));
-    int e0 = 0;
-    while (e0 < nE) {
-        int nb = 0;
-        size_t need = 0;
-        int cap = c->opts.batch > 0 ? c->opts.batch : 1 << 30;
-        while (e0 + nb < nE && nb < cap) {
-            size_t pe = per_energy(e0 + nb);
-            if (nb > 0 && need + pe > budget) break;
-            need += pe;
-            ++nb;
-        }
-        if (need > budget) return fail(c, PWQT_ERR_OOM, "one energy needs " + std::to_string(need) + " bytes, budget " + std::to_string(budget));
-        // workspace
-        std::vector<size_t> off(nb + 1, 0);
-        for (int b = 0; b < nb; ++b) off[b + 1] = off[b] + (size_t)N * n * (n + ms[e0 + b] + md[e0 + b]);
+
+    // One group of energies [g0, g0 + gn) of a batch, on stream gs: job tables, the sweep
+    // (FP64 kernel, or the mixed path with its refinement on lane L) and the observables.
+    // obs receives the group's observable descriptors (solution pointers for the density).
+    auto group = [&](int g0, int gn, Lane* L, cudaStream_t gs, std::vector<ObsJob>& obs) -> int {
+        std::vector<size_t> off(gn + 1, 0);
+        for (int b = 0; b < gn; ++b) off[b + 1] = off[b] + (size_t)N * n * (n + ms[g0 + b] + md[g0 + b]);
         size_t maxm = 1;
-        for (int b = 0; b < nb; ++b) maxm = std::max<size_t>(maxm, ms[e0 + b] + md[e0 + b]);
-        DBuf &XY = c->ws_xy, &Sb = c->ws_s, &jobs_d = c->ws_jobs, &obs_d = c->ws_obs, &res_d = c->ws_res, &norms = c->ws_norms;
+        for (int b = 0; b < gn; ++b) maxm = std::max<size_t>(maxm, ms[g0 + b] + md[g0 + b]);
+        DBuf &XY = c->ws_xy, &Sb = c->ws_s;
+        DBuf &jobs_d = L ? L->ws_jobs : c->ws_jobs, &obs_d = L ? L->ws_obs : c->ws_obs, &res_d = L ? L->ws_res : c->ws_res,
+             &norms = L ? L->ws_norms : c->ws_norms;
         if (precision == PWQT_FP64) {
-            PWQT_TRY(ensure(c, XY, sizeof(double2) * std::max<size_t>(off[nb], 1)));
-            PWQT_TRY(ensure(c, Sb, sizeof(double2) * nn * nb));
+            PWQT_TRY(ensure(c, XY, sizeof(double2) * std::max<size_t>(off[gn], 1)));
+            PWQT_TRY(ensure(c, Sb, sizeof(double2) * nn * gn));
         }
-        PWQT_TRY(ensure(c, norms, sizeof(double) * 2 * nb * maxm));
-        PWQT_CUDA(c, cudaMemsetAsync(norms.p, 0, sizeof(double) * 2 * nb * maxm, st));
-        std::vector<SweepJob> jobs(nb);
-        std::vector<ObsJob> obs(nb);
-        std::vector<ResJob> res(nb);
-        for (int b = 0; b < nb; ++b) {
-            int e = e0 + b;
+        PWQT_TRY(ensure(c, norms, sizeof(double) * 2 * gn * maxm));
+        PWQT_CUDA(c, cudaMemsetAsync(norms.p, 0, sizeof(double) * 2 * gn * maxm, gs));
+        std::vector<SweepJob> jobs(gn);
+        obs.assign(gn, ObsJob{});
+        std::vector<ResJob> res(gn);
+        for (int b = 0; b < gn; ++b) {
+            int e = g0 + b;
             LeadEntry *Ls = ls[e], *Ld = ld[e];
             int m = ms[e] + md[e];
             SweepJob& J = jobs[b];
@@ -269,45 +264,101 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
             Rj.resid = o.resid + e;
         }
         // statuses from the contacts
-        for (int b = 0; b < nb; ++b)
-            PWQT_CUDA(c, cudaMemcpyAsync(o.status + e0 + b, &hst[e0 + b], sizeof(int), cudaMemcpyHostToDevice, st));
-        PWQT_TRY(ensure(c, jobs_d, sizeof(SweepJob) * nb));
-        PWQT_TRY(ensure(c, obs_d, sizeof(ObsJob) * nb));
-        PWQT_TRY(ensure(c, res_d, sizeof(ResJob) * nb));
-        PWQT_CUDA(c, cudaMemcpyAsync(jobs_d.p, jobs.data(), sizeof(SweepJob) * nb, cudaMemcpyHostToDevice, st));
-        PWQT_CUDA(c, cudaMemcpyAsync(obs_d.p, obs.data(), sizeof(ObsJob) * nb, cudaMemcpyHostToDevice, st));
-        PWQT_CUDA(c, cudaMemcpyAsync(res_d.p, res.data(), sizeof(ResJob) * nb, cudaMemcpyHostToDevice, st));
+        PWQT_CUDA(c, cudaMemcpyAsync(o.status + g0, &hst[g0], sizeof(int) * gn, cudaMemcpyHostToDevice, gs));
+        PWQT_TRY(ensure(c, jobs_d, sizeof(SweepJob) * gn));
+        PWQT_TRY(ensure(c, obs_d, sizeof(ObsJob) * gn));
+        PWQT_TRY(ensure(c, res_d, sizeof(ResJob) * gn));
+        PWQT_CUDA(c, cudaMemcpyAsync(jobs_d.p, jobs.data(), sizeof(SweepJob) * gn, cudaMemcpyHostToDevice, gs));
+        PWQT_CUDA(c, cudaMemcpyAsync(obs_d.p, obs.data(), sizeof(ObsJob) * gn, cudaMemcpyHostToDevice, gs));
+        PWQT_CUDA(c, cudaMemcpyAsync(res_d.p, res.data(), sizeof(ResJob) * gn, cudaMemcpyHostToDevice, gs));
         if (precision != PWQT_FP64) {
-            PWQT_TRY(solve_mixed(c, s, sys, jobs, jobs_d.as<SweepJob>(), res, res_d.as<ResJob>(), obs, obs_d.as<ObsJob>(), nb,
-                                 o.iters + e0, st, precision == PWQT_MIXED));
+            PWQT_TRY(solve_mixed(c, s, sys, jobs, jobs_d.as<SweepJob>(), res, res_d.as<ResJob>(), obs, obs_d.as<ObsJob>(), gn,
+                                 o.iters + g0, gs, precision == PWQT_MIXED, *L));
         } else {
-            if (c->profile) PWQT_CUDA(c, cudaEventRecord(c->ev0, st));
-            launch_sweep_fp64(sys, jobs_d.as<SweepJob>(), nb, st);
+            if (c->profile) PWQT_CUDA(c, cudaEventRecord(c->ev0, gs));
+            launch_sweep_fp64(sys, jobs_d.as<SweepJob>(), gn, gs);
             c->launches++;
             if (c->profile) {
-                PWQT_CUDA(c, cudaEventRecord(c->ev1, st));
+                PWQT_CUDA(c, cudaEventRecord(c->ev1, gs));
                 PWQT_CUDA(c, cudaEventSynchronize(c->ev1));
-                float ms = 0;
-                cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-                c->prof_ms += ms;
+                float msec = 0;
+                cudaEventElapsedTime(&msec, c->ev0, c->ev1);
+                c->prof_ms += msec;
                 c->prof_launches += 1;
-                c->prof_flops += (56.0 / 3.0) * (double)N * n * n * (double)n * nb;
+                c->prof_flops += (56.0 / 3.0) * (double)N * n * n * (double)n * gn;
             }
             PWQT_CUDA(c, cudaGetLastError());
-            launch_residual_fp64(sys, res_d.as<ResJob>(), nb, st);
+            launch_residual_fp64(sys, res_d.as<ResJob>(), gn, gs);
             c->launches += 2;
             if (o.iters) {
-                k_fill_int<<<(nb + 127) / 128, 128, 0, st>>>(o.iters + e0, 0, nb);
+                k_fill_int<<<(gn + 127) / 128, 128, 0, gs>>>(o.iters + g0, 0, gn);
                 c->launches++;
             }
         }
-        launch_observables(n, N, obs_d.as<ObsJob>(), nb, st);
+        launch_observables(n, N, obs_d.as<ObsJob>(), gn, gs);
         c->launches += 2;
         PWQT_CUDA(c, cudaGetLastError());
+        PWQT_CUDA(c, cudaStreamSynchronize(gs));
+        return PWQT_OK;
+    };
+
+    int e0 = 0;
+    while (e0 < nE) {
+        int nb = 0;
+        size_t need = 0;
+        int cap = c->opts.batch > 0 ? c->opts.batch : 1 << 30;
+        while (e0 + nb < nE && nb < cap) {
+            size_t pe = per_energy(e0 + nb);
+            if (nb > 0 && need + pe > budget) break;
+            need += pe;
+            ++nb;
+        }
+        if (need > budget) return fail(c, PWQT_ERR_OOM, "one energy needs " + std::to_string(need) + " bytes, budget " + std::to_string(budget));
+        std::vector<ObsJob> obs_a, obs_b;
+        int split = nb;
+        if (precision == PWQT_FP64) {
+            PWQT_TRY(group(e0, nb, nullptr, st, obs_a));
+        } else {
+            PWQT_TRY(c->lanes[0].init(c->dev) == PWQT_OK ? PWQT_OK : fail(c, PWQT_ERR_CUDA, "lane stream"));
+            if (nb >= 16) {
+                // two halves on two lanes (streams, host threads): the GPU runs one half's
+                // float-float residual beside the other half's latency-bound kernels
+                PWQT_TRY(c->lanes[1].init(c->dev) == PWQT_OK ? PWQT_OK : fail(c, PWQT_ERR_CUDA, "lane stream"));
+                split = nb / 2;
+                PWQT_CUDA(c, cudaStreamSynchronize(st));   // work the halves depend on (zero block)
+                int rc_b = PWQT_OK;
+                std::thread tb([&] {
+                    cudaSetDevice(c->dev);
+                    rc_b = group(e0 + split, nb - split, &c->lanes[1], c->lanes[1].st, obs_b);
+                });
+                const int rc_a = group(e0, split, &c->lanes[0], c->lanes[0].st, obs_a);
+                tb.join();
+                PWQT_TRY(rc_a);
+                PWQT_TRY(rc_b);
+            } else {
+                PWQT_TRY(group(e0, nb, &c->lanes[0], st, obs_a));
+            }
+            // the lanes' profile counters into the context's: times, flops and launches add up
+            // (per-lane rates stay per launch); the halves refine in parallel, so a batch counts
+            // the larger of their iteration counts
+            long long it_max = 0;
+            for (auto& L : c->lanes) {
+                c->prof_ms += L.prof_ms; c->prof_flops += L.prof_flops; c->prof_launches += L.prof_launches;
+                c->prof_phase_ms[0] += L.prof_phase_ms[0]; c->prof_phase_ms[1] += L.prof_phase_ms[1];
+                it_max = std::max(it_max, L.prof_ir_iters);
+                L.prof_ms = L.prof_flops = L.prof_phase_ms[0] = L.prof_phase_ms[1] = 0;
+                L.prof_launches = L.prof_ir_iters = 0;
+            }
+            c->prof_ir_iters += it_max;
+        }
         if (dens) {
             DensityAcc d = *dens;
             d.w = dens->w + e0;
-            PWQT_TRY(density_accumulate_batch(c, s, obs, E + e0, d, nb, st));
+            PWQT_TRY(density_accumulate_batch(c, s, obs_a, E + e0, d, split, st));
+            if (split < nb) {
+                d.w = dens->w + e0 + split;
+                PWQT_TRY(density_accumulate_batch(c, s, obs_b, E + e0 + split, d, nb - split, st));
+            }
         }
         // n_open (source, drain) per energy
         std::vector<int> nopen(2 * nb);

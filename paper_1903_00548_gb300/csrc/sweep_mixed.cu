@@ -511,7 +511,8 @@ size_t mixed_bytes_per_energy(int n, int N, int m) {
 }
 
 int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJob>& jobs, SweepJob* jobs_d, std::vector<ResJob>& res,
-                ResJob* res_d, std::vector<ObsJob>& obs, ObsJob* obs_d, int nb, int* iters_dev, cudaStream_t st, bool refine) {
+                ResJob* res_d, std::vector<ObsJob>& obs, ObsJob* obs_d, int nb, int* iters_dev, cudaStream_t st, bool refine,
+                Lane& L) {
     // idempotent (a function attribute of the device): set per call, no flag shared between host threads
     if (cgemm_tc_init() != 0) return fail(c, PWQT_ERR_CUDA, "tensor-core GEMM set-up failed");
     const int n = sys.n, N = sys.N;
@@ -529,8 +530,8 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
     S.sL = (long long)n * std::max(n, m);   // L_i (n x n), reused as the n x m correction scratch
     S.sC = (long long)N * n * m;
     const size_t bytes = mixed_bytes_per_energy(n, N, m) * nb + 1024 * 4;
-    PWQT_TRY(ensure(c, c->ws_mixed, bytes));
-    char* base = c->ws_mixed.as<char>();
+    PWQT_TRY(ensure(c, L.ws_mixed, bytes));
+    char* base = L.ws_mixed.as<char>();
     auto take = [&](size_t b) { char* p = base; base += (b + 255) / 256 * 256; return p; };
     S.F = (float2*)take(sizeof(float2) * S.sF * nb);
     S.XY = (float2*)take(sizeof(float2) * S.sXY * nb);
@@ -571,7 +572,7 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         launch_cgemm_tc(g, nb, M, Nc, K, st);
         c->launches++;
     };
-    if (c->profile) PWQT_CUDA(c, cudaEventRecord(c->ev0, st));
+    if (c->profile) PWQT_CUDA(c, cudaEventRecord(L.ev[0], st));
     for (int i = 0; i < N; ++i) {
         float2* Fi = S.F + (size_t)i * n * n;
         float2* XYi = S.XY + (size_t)i * n * w;
@@ -605,13 +606,13 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         gemm(XYi, S.sXY, w, XYn + n, S.sXY, w, XYn + n, S.sXY, w, XYi + n, S.sXY, w, XYi + n, S.sXY, w, m, n, m, n);
     }
     if (c->profile) {
-        PWQT_CUDA(c, cudaEventRecord(c->ev1, st));
-        PWQT_CUDA(c, cudaEventSynchronize(c->ev1));
+        PWQT_CUDA(c, cudaEventRecord(L.ev[1], st));
+        PWQT_CUDA(c, cudaEventSynchronize(L.ev[1]));
         float ms = 0;
-        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-        c->prof_ms += ms;
-        c->prof_launches += 1;
-        c->prof_flops += (56.0 / 3.0) * (double)N * n * n * (double)n * nb;
+        cudaEventElapsedTime(&ms, L.ev[0], L.ev[1]);
+        L.prof_ms += ms;
+        L.prof_launches += 1;
+        L.prof_flops += (56.0 / 3.0) * (double)N * n * n * (double)n * nb;
     }
     PWQT_CUDA(c, cudaGetLastError());
     if (cgemm_tc_error(true, st)) return fail(c, PWQT_ERR_TIMEOUT, "tensor-core GEMM: a bounded mbarrier wait gave up");
@@ -636,20 +637,20 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
     const double tol = c->opts.ir_tol;
     PWQT_CUDA(c, cudaMemcpyAsync(active_d, active.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
     for (int it = 0;; ++it) {
-        if (c->profile) PWQT_CUDA(c, cudaEventRecord(c->ev0, st));
+        if (c->profile) PWQT_CUDA(c, cudaEventRecord(L.ev[0], st));
         PWQT_CUDA(c, cudaMemsetAsync(res[0].rn2, 0, sizeof(double) * 2 * (size_t)nb * m, st));
         launch_residual_ff(RF, res_d, nb, m, active_d, st);   // energies still refining
         c->launches += 3;
-        if (c->profile) PWQT_CUDA(c, cudaEventRecord(c->ev1, st));
+        if (c->profile) PWQT_CUDA(c, cudaEventRecord(L.ev[1], st));
         PWQT_CUDA(c, cudaMemcpyAsync(resid.data(), res[0].resid, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
         PWQT_CUDA(c, cudaStreamSynchronize(st));
         if (c->profile) {
             float ms = 0;
-            cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-            c->prof_phase_ms[0] += ms;
+            cudaEventElapsedTime(&ms, L.ev[0], L.ev[1]);
+            L.prof_phase_ms[0] += ms;
             if (it > 0) {
-                cudaEventElapsedTime(&ms, c->ev2, c->ev3);
-                c->prof_phase_ms[1] += ms;
+                cudaEventElapsedTime(&ms, L.ev[2], L.ev[3]);
+                L.prof_phase_ms[1] += ms;
             }
         }
         int any = 0;
@@ -677,8 +678,8 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         }
         if (!any) break;
         if (c->profile) {
-            PWQT_CUDA(c, cudaEventRecord(c->ev2, st));
-            c->prof_ir_iters++;
+            PWQT_CUDA(c, cudaEventRecord(L.ev[2], st));
+            L.prof_ir_iters++;
         }
         PWQT_CUDA(c, cudaMemcpyAsync(active_d, active.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
         for (int i = 0; i < N; ++i) {
@@ -701,7 +702,7 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         }
         k_mx_update<<<dim3(256, nb), NT, 0, st>>>(S, active_d);
         c->launches++;
-        if (c->profile) PWQT_CUDA(c, cudaEventRecord(c->ev3, st));
+        if (c->profile) PWQT_CUDA(c, cudaEventRecord(L.ev[3], st));
         PWQT_CUDA(c, cudaGetLastError());
     }
     PWQT_CUDA(c, cudaMemcpyAsync(iters_dev, iters.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));

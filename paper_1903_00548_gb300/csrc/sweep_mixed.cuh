@@ -43,6 +43,6 @@ void launch_residual_finish(const ResJob* jobs, int nb, cudaStream_t st, const i
 size_t mixed_bytes_per_energy(int n, int N, int m);
 int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJob>& jobs, SweepJob* jobs_d,
                 std::vector<ResJob>& res, ResJob* res_d, std::vector<ObsJob>& obs, ObsJob* obs_d, int nb, int* iters_dev,
-                cudaStream_t st, bool refine = true);
+                cudaStream_t st, bool refine, Lane& lane);
 
 }  // namespace pwqt
