@@ -829,6 +829,22 @@ def caroli_transmission(blk, Vd, Vu, U, E, cache=None, contacts=None):
     return float(np.trace(Gd @ X @ Gs @ X.conj().T).real)
 
 
+
+def green_diagonal(blk, Vd, Vu, U, E, cache=None, contacts=None):
+    """Diagonal blocks G_ii of the retarded Green's function G = [E M - H - V^e -
+    Sigma]^{-1} (the NEGF form of Sec. 3.2) and the node spectral density
+    -(2/pi) Im Tr G_ii.  By definition: the inverse of the assembled global matrix
+    (dense; N n <= 4000), then its diagonal blocks.  Returns (G_diag (N, n, n),
+    node_dos (N,))."""
+    N, n = Vd.shape[0], blk["n"]
+    if N * n > 4000:
+        raise ValueError("green_diagonal takes N n <= 4000 (dense inverse)")
+    cs, cd = contacts if contacts is not None else contacts_at(blk, E, float(U[0]), float(U[-1]), cache)
+    G = np.linalg.inv(global_matrix(blk, Vd, Vu, E, cs.Sigma, cd.Sigma))
+    Gd = np.stack([G[i * n:(i + 1) * n, i * n:(i + 1) * n] for i in range(N)])
+    dos = -(2.0 / math.pi) * np.array([np.trace(b).imag for b in Gd])
+    return Gd, dos
+
 # =============================================================================
 # Sec. 4 (self-consistent loop): non-linear Poisson by Newton with the semi-classical
 # Jacobian and DIIS, on a 1D finite-element model along z
