@@ -328,6 +328,25 @@ int pwqt_density_grid(pwqt_ctx* ctx, int sys, int nx, int nz, double* n_r);
 int pwqt_transmission_caroli(pwqt_ctx* ctx, int sys, int n_E, const double* E, double* T, int* status);
 
 /*
+ * Diagonal blocks of the retarded Green's function G = [E M - H - V^e - Sigma]^{-1}
+ * (Sec. 3.2, the NEGF form of the open-boundary problem; Sigma = Sigma_s + Sigma_d on
+ * the end nodes) by the recursive Green's-function recursion over the nodes: the
+ * FP64 block sweep's forward elimination with [U_i | I] at every node gives X_i and
+ * the left-connected g_i = S_i^{-1}; the backward pass forms G_{N-1} = g_{N-1},
+ * G_i = g_i + (X_i G_{i+1})(U_i^H g_i).  Outputs (host, caller-owned):
+ *   node_dos [n_E x N]: -(2/pi) Im Tr G_ii, the node spectral density; in a
+ *       ballistic device it equals the sum of the source- and drain-injected node
+ *       densities node_n of pwqt_solve (Sec. 3.3), with no mode decomposition inside
+ *       the device;
+ *   G_diag [n_E x N x n x n x 2] (may be NULL): the blocks G_ii, row-major,
+ *       complex128 interleaved;
+ *   status [n_E] (may be NULL): the PWQT_ST_* bits of the contacts and the sweep.
+ * Work per energy ~2.5x the FP64 sweep with n injected columns, device memory
+ * ~N n^2 32 bytes per energy of a batch.  Errors: as pwqt_solve.
+ */
+int pwqt_green_diagonal(pwqt_ctx* ctx, int sys, int n_E, const double* E, double* node_dos, double* G_diag, int* status);
+
+/*
  * Energy integrals by adaptive Simpson quadrature (Sec. 3.3: the density integral
  * is evaluated adaptively to a tolerance, with the error estimated on the node
  * density; Eq. current: the ballistic current with the same method).  Integrands:

@@ -24,6 +24,7 @@ struct SweepJob {
     double2* XY;                // N x n x (n + m): [X_i | y_i], y overwritten by c_i
     double2* S;                 // n x n scratch
     int* status;
+    double* dos;                // Green's-function recursion only: N node spectral densities
 };
 
 // Reduction descriptors of one energy (observables of Eq. transmission and Sec. 3.3).
@@ -43,6 +44,10 @@ struct ObsJob {
 };
 
 void launch_sweep_fp64(const SweepSys& sys, const SweepJob* jobs, int nb, cudaStream_t st);
+// Diagonal blocks of G = [E M - H - Sigma]^{-1} by the recursive Green's-function
+// recursion over the nodes (jobs with ms = n, md = 0; XY holds N x n x 2n):
+// on return XY_i = [* | G_ii] and dos[i] = -(2/pi) Im Tr G_ii.
+void launch_green_fp64(const SweepSys& sys, const SweepJob* jobs, int nb, cudaStream_t st);
 void launch_observables(int n, int N, const ObsJob* jobs, int nb, cudaStream_t st);
 // rank-m updates of the density matrix from one batch of solved energies (density.cu);
 // E and the weights in d.w are this batch's

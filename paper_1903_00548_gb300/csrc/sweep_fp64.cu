@@ -81,6 +81,75 @@ __device__ int cta_pivot(const double2* S, int lds, int n, int j) {
     return p;
 }
 
+// -(2/pi) Im Tr of the n x n block at G (row stride ldg), block-wide; thread 0 gets it
+__device__ double cta_dos(const double2* G, int ldg, int n) {
+    __shared__ double part[NT / 32];
+    double acc = 0.0;
+    for (int r = threadIdx.x; r < n; r += NT) acc += G[(size_t)r * ldg + r].y;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffff, acc, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < NT / 32; ++w) t += part[w];
+    __syncthreads();
+    return -(2.0 / 3.141592653589793) * t;
+}
+
+// Backward pass of the Green's-function recursion over the forward panels
+// R_i = [X_i | g_i] (row stride 2n).  Per node, with the n x n scratch S:
+//   S = -X_i G_{i+1};  X-part of R_i = -L_{i+1} g_i;  g-part of R_i -= (-S)(X-part)
+// so that the g-part becomes g_i + (X_i G_{i+1})(L_{i+1} g_i) = G_i.
+__device__ void green_backward(const SweepSys& sys, const SweepJob& J, double2* smem, int st) {
+    const int n = sys.n, N = sys.N, w = 2 * n;
+    const double E = J.E;
+    double2* S = J.S;
+    double d = cta_dos(J.XY + (size_t)(N - 1) * n * w + n, w, n);
+    if (threadIdx.x == 0) J.dos[N - 1] = d;
+    for (int i = N - 2; i >= 0; --i) {
+        double2* R = J.XY + (size_t)i * n * w;
+        const double2* Gn = J.XY + (size_t)(i + 1) * n * w + n;
+        for (int t = threadIdx.x; t < n * n; t += NT) S[t] = make_double2(0, 0);
+        __syncthreads();
+        {
+            auto A = [&](int r, int k) { return R[(size_t)r * w + k]; };
+            auto C = [&](int r, int cc) -> double2* { return S + (size_t)r * n + cc; };
+            cta_gemm_sub(smem, n, n, n, A, Gn, w, C);                 // S = -X_i G_{i+1}
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < n * n; t += NT) R[(size_t)(t / n) * w + t % n] = make_double2(0, 0);
+        __syncthreads();
+        {
+            const double2* HV1 = sys.HV1 + (size_t)i * n * n;
+            const double2* M1 = sys.M1;
+            auto A = [&](int r, int k) {                               // L_{i+1}[r][k] = conj(U_i[k][r])
+                size_t t = (size_t)k * n + r;
+                return cconj(csub(cscale(M1[t], E), HV1[t]));
+            };
+            auto C = [&](int r, int cc) -> double2* { return R + (size_t)r * w + cc; };
+            cta_gemm_sub(smem, n, n, n, A, R + n, w, C);             // X-part = -L_{i+1} g_i
+        }
+        __syncthreads();
+        {
+            auto A = [&](int r, int k) { const double2 v = S[(size_t)r * n + k]; return make_double2(-v.x, -v.y); };
+            auto C = [&](int r, int cc) -> double2* { return R + (size_t)r * w + n + cc; };
+            cta_gemm_sub(smem, n, n, n, A, R, w, C);                 // g-part -= (X_i G_{i+1})(-L_{i+1} g_i)
+        }
+        __syncthreads();
+        d = cta_dos(R + n, w, n);
+        if (threadIdx.x == 0) J.dos[i] = d;
+    }
+    if (threadIdx.x == 0) atomicOr(J.status, st);
+}
+
+// GREEN = false: the QTBM solve of the file header.  GREEN = true: the recursive Green's-function
+// form of the same elimination (the NEGF side of Sec. 3.2).  The forward pass is the
+// sweep with [U_i | I] as every node's right-hand side and no coupling between the
+// right-hand sides of neighbouring nodes, so that R_i = [X_i | g_i] with the
+// left-connected g_i = S_i^{-1}; the backward pass then forms the diagonal blocks
+//     G_{N-1} = g_{N-1},   G_i = g_i + (X_i G_{i+1}) (L_{i+1} g_i)
+// in place of g_i, with L_{i+1} = U_i^H, and records -(2/pi) Im Tr G_i.
+template <bool GREEN>
 __global__ void __launch_bounds__(NT) k_sweep_fp64(SweepSys sys, const SweepJob* __restrict__ jobs) {
     const SweepJob J = jobs[blockIdx.x];
     const int n = sys.n, N = sys.N, m = J.ms + J.md, w = n + m;
@@ -105,6 +174,8 @@ __global__ void __launch_bounds__(NT) k_sweep_fp64(SweepSys sys, const SweepJob*
             double2 v = make_double2(0, 0);
             if (cc < n) {
                 if (i < N - 1) v = csub(cscale(sys.M1[(size_t)r * n + cc], E), HV1[(size_t)r * n + cc]);
+            } else if (GREEN) {
+                if (cc - n == r) v = make_double2(1.0, 0.0);
             } else {
                 int col = cc - n;
                 if (i == 0 && col < J.ms) v = J.rhs_s[(size_t)r * J.ms + col];
@@ -123,7 +194,8 @@ __global__ void __launch_bounds__(NT) k_sweep_fp64(SweepSys sys, const SweepJob*
                 return cconj(csub(cscale(M1[t], E), HVp[t]));
             };
             auto C = [&](int r, int cc) -> double2* { return cc < n ? S + (size_t)r * n + cc : R + (size_t)r * w + cc; };
-            cta_gemm_sub(smem, n, w, n, A, P, w, C);   // [S | *, y] -= L_i [X_{i-1} | y_{i-1}]  (cols n..w-1 of R)
+            // [S | *, y] -= L_i [X_{i-1} | y_{i-1}]  (cols n..w-1 of R); S alone for GREEN
+            cta_gemm_sub(smem, n, GREEN ? n : w, n, A, P, w, C);
             __syncthreads();
         }
         // Gaussian elimination with partial pivoting on S, applied to the rows of R
@@ -170,20 +242,28 @@ __global__ void __launch_bounds__(NT) k_sweep_fp64(SweepSys sys, const SweepJob*
             __syncthreads();
         }
     }
-    // back substitution over nodes: c_i = y_i - X_i c_{i+1} (c overwrites y)
-    for (int i = N - 2; i >= 0; --i) {
-        double2* R = J.XY + (size_t)i * n * w;
-        const double2* Cn = J.XY + (size_t)(i + 1) * n * w + n;
-        auto A = [&](int r, int k) { return R[(size_t)r * w + k]; };
-        auto C = [&](int r, int cc) -> double2* { return R + (size_t)r * w + n + cc; };
-        cta_gemm_sub(smem, n, m, n, A, Cn, w, C);
-        __syncthreads();
+    if constexpr (GREEN) {
+        green_backward(sys, J, smem, st);
+    } else {
+        // back substitution over nodes: c_i = y_i - X_i c_{i+1} (c overwrites y)
+        for (int i = N - 2; i >= 0; --i) {
+            double2* R = J.XY + (size_t)i * n * w;
+            const double2* Cn = J.XY + (size_t)(i + 1) * n * w + n;
+            auto A = [&](int r, int k) { return R[(size_t)r * w + k]; };
+            auto C = [&](int r, int cc) -> double2* { return R + (size_t)r * w + n + cc; };
+            cta_gemm_sub(smem, n, m, n, A, Cn, w, C);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) atomicOr(J.status, st);
     }
-    if (threadIdx.x == 0) atomicOr(J.status, st);
 }
 
 void launch_sweep_fp64(const SweepSys& sys, const SweepJob* jobs, int nb, cudaStream_t st) {
-    k_sweep_fp64<<<nb, NT, 0, st>>>(sys, jobs);
+    k_sweep_fp64<false><<<nb, NT, 0, st>>>(sys, jobs);
+}
+
+void launch_green_fp64(const SweepSys& sys, const SweepJob* jobs, int nb, cudaStream_t st) {
+    k_sweep_fp64<true><<<nb, NT, 0, st>>>(sys, jobs);
 }
 
 }  // namespace pwqt

@@ -30,7 +30,7 @@ EXPORTS = ["pwqt_create", "pwqt_destroy", "pwqt_last_error", "pwqt_assemble_intr
            "pwqt_profile_refinement", "pwqt_set_refinement", "pwqt_solve_multi",
            "pwqt_server_create", "pwqt_server_add_basis", "pwqt_server_submit", "pwqt_server_wait",
            "pwqt_server_stats", "pwqt_server_last_error", "pwqt_server_destroy", "pwqt_integrate",
-           "pwqt_transmission_caroli", "pwqt_self_consistent"]
+           "pwqt_transmission_caroli", "pwqt_self_consistent", "pwqt_green_diagonal"]
 
 
 class PwqtError(RuntimeError):
@@ -114,6 +114,7 @@ def load(path: str = LIB_PATH):
     lib.pwqt_server_destroy.argtypes = [P]
     lib.pwqt_integrate.argtypes = [P, I, I, D, D, D, D, D, D, I, I, I, dp, dp, ip, dp, dp, ip, I]
     lib.pwqt_transmission_caroli.argtypes = [P, I, I, dp, dp, ip]
+    lib.pwqt_green_diagonal.argtypes = [P, I, I, dp, dp, dp, ip]
     lib.pwqt_self_consistent.argtypes = [P, I, C.POINTER(Poisson1DC), D, D, D, D, D, D, D, I, I, I, dp, dp, ip, dp]
     lib.pwqt_accumulate_density.argtypes = [P, I, I, dp, dp, D, D, D, I, ip]
     lib.pwqt_get_density_matrix.argtypes = [P, I, dp, dp]
@@ -331,6 +332,18 @@ class Context:
         st = np.zeros(len(E), np.int32)
         self._check(self.lib.pwqt_transmission_caroli(self.h, sys, len(E), _dptr(E), _dptr(T), _iptr(st)))
         return T, st
+
+    def green_diagonal(self, sys: int, E, blocks: bool = False):
+        """(node_dos [n_E, N], G_diag [n_E, N, n, n] complex or None, status) from the
+        recursive Green's function."""
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        N = self.n_nodes.get(sys, 1)   # an unknown system is reported by the library
+        dos = np.zeros((len(E), N))
+        G = np.zeros((len(E), N, self.n, self.n), np.complex128) if blocks else None
+        st = np.zeros(len(E), np.int32)
+        gp = G.ctypes.data_as(C.POINTER(C.c_double)) if blocks else None
+        self._check(self.lib.pwqt_green_diagonal(self.h, sys, len(E), _dptr(E), _dptr(dos), gp, _iptr(st)))
+        return dos, G, st
 
     def density_reset(self, sys: int):
         self._check(self.lib.pwqt_density_reset(self.h, sys))
