@@ -317,10 +317,15 @@ __global__ void k_mx_load_r(MixSys S, int i, const int* __restrict__ active) {
 // w <- U^{-1} L^{-1} P w for node i.  The m right-hand sides are independent, so
 // every energy gets ceil(m / LC) CTAs of LC columns each; a CTA keeps its columns
 // in shared memory (n x LC), solves each 32-row diagonal block with one warp per
-// two columns (lane = row, the solved value broadcast by shuffle) and applies the
+// LC / 8 columns (lane = row, the solved value broadcast by shuffle) and applies the
 // off-diagonal part of the factors to the rows below (forward) or above
-// (backward) in parallel over (row, column).
-constexpr int LC = 16;
+// (backward) in parallel over (row, column).  The solve is latency-bound (a chain
+// of 2 n / 32 block steps per CTA), so LC is small: at n = 512 a CTA holds ~59 KB
+// of shared memory, three fit on an SM, and a node's launch is one wave of
+// ceil(m / 8) CTAs per energy.
+constexpr int LC = 8;
+constexpr int LCW = LC / (NT / 32);   // columns per warp in the diagonal-block solves
+static_assert(LC % (NT / 32) == 0, "every warp takes the same number of columns");
 
 __device__ __forceinline__ float2 shfl2(float2 v, int src) {
     return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
@@ -425,7 +430,7 @@ __global__ void __launch_bounds__(NT) k_mx_lusolve(MixSys S, int i, const int* _
             }
         }
         __syncthreads();
-        for (int cc = 2 * warp; cc < 2 * warp + 2; ++cc) {
+        for (int cc = LCW * warp; cc < LCW * (warp + 1); ++cc) {
             float2 v = lane < wd ? T[(kb + lane) * LC + cc] : make_float2(0.f, 0.f);
             for (int j = 0; j + 1 < wd; ++j) {
                 const float2 aj = shfl2(v, j);
@@ -456,7 +461,7 @@ __global__ void __launch_bounds__(NT) k_mx_lusolve(MixSys S, int i, const int* _
             }
         }
         __syncthreads();
-        for (int cc = 2 * warp; cc < 2 * warp + 2; ++cc) {
+        for (int cc = LCW * warp; cc < LCW * (warp + 1); ++cc) {
             float2 v = lane < wd ? T[(kb + lane) * LC + cc] : make_float2(0.f, 0.f);
             for (int j = wd - 1; j >= 0; --j) {
                 if (lane == j) {
