@@ -38,7 +38,6 @@ struct MixSys {
     const SweepJob* jobs;
 };
 
-__device__ __forceinline__ float2 fmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ void ffma(float2& a, float2 b, float2 c) {
     a.x = fmaf(b.x, c.x, fmaf(-b.y, c.y, a.x));
     a.y = fmaf(b.x, c.y, fmaf(b.y, c.x, a.y));
@@ -391,21 +390,10 @@ __global__ void __launch_bounds__(NT) k_mx_lusolve(MixSys S, int i, const int* _
     float2* Fs = Ld + PW * (PW + 1);                                                     // LR x (PW+1)
     float2* T = Fs + LR * (PW + 1);                                                      // n x LC
     const float2* F = S.F + e * S.sF + (size_t)i * n * n;
-    const int* piv = S.piv + e * S.sP + (size_t)i * n;
+    const int* pg = S.piv + e * S.sP + (size_t)i * n;        // row permutation (k_mx_perm)
     float2* W = S.XY + e * S.sXY + (size_t)i * n * w + n;     // row stride w
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    // compose the pivots into a permutation: stage them in shared memory (T is free
-    // until it is loaded below) so the serial composition reads no global memory
-    int* pv = reinterpret_cast<int*>(T);
-    for (int j = t; j < n; j += NT) pv[j] = piv[j];
-    __syncthreads();
-    if (t == 0) {
-        for (int j = 0; j < n; ++j) perm[j] = j;
-        for (int j = 0; j < n; ++j) {
-            const int p = pv[j];
-            if (p != j) { int a = perm[j]; perm[j] = perm[p]; perm[p] = a; }
-        }
-    }
+    for (int j = t; j < n; j += NT) perm[j] = pg[j];
     __syncthreads();
 #pragma unroll 8
     for (int q = t; q < n * LC; q += NT) {
@@ -484,6 +472,27 @@ __global__ void __launch_bounds__(NT) k_mx_lusolve(MixSys S, int i, const int* _
         const int r = q / LC, g = q % LC;
         if (c0 + g < m) W[(size_t)r * w + c0 + g] = T[q];
     }
+}
+
+// Once per factorisation: the pivot rows of node i (row j exchanged with piv[j], in
+// order j = 0..n-1) composed into the row permutation, P w = w[perm[.]], written over
+// the pivots, so that the correction solves of every refinement step read it directly.
+// Grid (energies, nodes), one warp; the composition is serial in shared memory.
+__global__ void k_mx_perm(MixSys S) {
+    const int e = blockIdx.x, i = blockIdx.y, n = S.n;
+    extern __shared__ int ps[];
+    int* pv = ps;          // n pivots
+    int* perm = ps + n;    // n
+    int* piv = S.piv + e * S.sP + (size_t)i * n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) { pv[j] = piv[j]; perm[j] = j; }
+    __syncwarp();
+    if (threadIdx.x == 0)
+        for (int j = 0; j < n; ++j) {
+            const int p = pv[j];
+            if (p != j) { const int a = perm[j]; perm[j] = perm[p]; perm[p] = a; }
+        }
+    __syncwarp();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) piv[j] = perm[j];
 }
 
 // c += d (FP64), active energies
@@ -622,7 +631,8 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
     PWQT_CUDA(c, cudaGetLastError());
     if (cgemm_tc_error(true, st)) return fail(c, PWQT_ERR_TIMEOUT, "tensor-core GEMM: a bounded mbarrier wait gave up");
     k_mx_to64<<<dim3(256, nb), NT, 0, st>>>(S);
-    c->launches++;
+    k_mx_perm<<<dim3(nb, N), 32, 2 * sizeof(int) * n, st>>>(S);
+    c->launches += 2;
 
     // ---------------- refinement with FP64 residuals
     for (int b = 0; b < nb; ++b) {
