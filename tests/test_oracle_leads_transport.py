@@ -191,3 +191,19 @@ def test_caroli_transmission_equals_mode_resolved():
             r = O.solve_energy(s.blk, s.Vd, s.Vu, s.U, E)
             Tc = O.caroli_transmission(s.blk, s.Vd, s.Vu, s.U, E)
             assert abs(Tc - r.T) <= 1e-9 * max(1.0, r.T) + 4 * abs(r.T - r.T_ds), (E, Tc, r.T)
+
+
+def test_block512_golden_values_are_physical():
+    # the stored block-512 expectations (tests/golden/make_block512.py) obey flux
+    # conservation and reciprocity, and the band cut of their basis is not degenerate
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "block512_n8.json")))
+    assert g["n"] == 512 and min(g["band_cut_gaps_eV"]) > 1e-3
+    for e in g["energies"]:
+        ms = e["n_open"][0]
+        assert ms == e["n_open"][1] and ms > 0
+        assert abs(e["T"] + e["R"] - ms) < 1e-8 * ms
+        assert abs(e["T"] - e["T_ds"]) < 1e-8 * ms
+        nn = np.array(e["node_n"])
+        assert nn.shape == (g["n_nodes"], 2) and np.all(nn > 0)
