@@ -10,7 +10,7 @@ complex64 block sweep on the tensor cores + refinement; --precision fp64 times t
 complex128 path.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                [--precision mixed|fp64|auto] [--batch B]
+                [--precision mixed|fp64|auto] [--batch B] [--clocks-csv PATH]
 Under torchrun every rank solves its own batch (weak scaling, no data-path
 collective); the timed region is bracketed by a barrier and synchronize and the
 max over ranks is reported.
@@ -275,8 +275,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize(dev)
     ctx.profile(True, reset=True)
     launches0 = ctx.kernel_launches()
-    clocks = Clocks(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-                    if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/pwqt_clocks_{rank}.csv")
+    clocks = Clocks(local, args.clocks_csv.format(rank=rank))
     barrier(world)
     torch.cuda.synchronize(dev)
     ev_s = torch.cuda.Event(enable_timing=True)
@@ -527,6 +526,8 @@ def main(argv=None):
     ap.add_argument("--no-density", action="store_true", help="skip the density-matrix timing")
     ap.add_argument("--serving", action="store_true", help="measure the serving loop instead of the headline metric")
     ap.add_argument("--requests", type=int, default=60, help="requests per serving pass")
+    ap.add_argument("--clocks-csv", default="/tmp/pwqt_clocks_{rank}.csv",
+                    help="where the nvidia-smi clock samples of the timed region are kept ({rank} is replaced)")
     args = ap.parse_args(argv)
     world, rank, local = dist_setup()
     if args.impl == "reference":
