@@ -341,8 +341,8 @@ int pwqt_transmission_caroli(pwqt_ctx* ctx, int sys, int n_E, const double* E, d
  *   G_diag [n_E x N x n x n x 2] (may be NULL): the blocks G_ii, row-major,
  *       complex128 interleaved;
  *   status [n_E] (may be NULL): the PWQT_ST_* bits of the contacts and the sweep.
- * Work per energy ~2.5x the FP64 sweep with n injected columns, device memory
- * ~N n^2 32 bytes per energy of a batch.  Errors: as pwqt_solve.
+ * Work per energy ~51 N n^3 real flops (2.7x the mode-resolved FP64 sweep), device
+ * memory ~N n^2 32 bytes per energy of a batch.  Errors: as pwqt_solve.
  */
 int pwqt_green_diagonal(pwqt_ctx* ctx, int sys, int n_E, const double* E, double* node_dos, double* G_diag, int* status);
 
