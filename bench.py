@@ -110,9 +110,6 @@ def _oracle_sample(conn, wl_name, n_nodes_full, reps):
     device shortened to ORACLE_SAMPLE_NODES nodes; its banded LU costs O(N), so the
     time of a full-length solve is t * N_full / N_sample.  One BLAS thread."""
     try:
-        os.environ["OPENBLAS_NUM_THREADS"] = "1"
-        os.environ["OMP_NUM_THREADS"] = "1"
-        os.environ["MKL_NUM_THREADS"] = "1"
         from oracle import pwqt_oracle as O
         from paper_1903_00548_gb300 import workloads as W
         wl = getattr(W, wl_name)()
@@ -133,11 +130,27 @@ def _oracle_sample(conn, wl_name, n_nodes_full, reps):
     conn.close()
 
 
+BLAS_THREAD_VARS = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+
+
 def start_oracle_sample(wl_name, n_nodes_full, reps=3):
+    # the spawned child imports numpy (and starts its BLAS threads) while it re-imports
+    # this module, before _oracle_sample runs: the one-thread setting must already be in
+    # the environment it inherits
     ctx = mp.get_context("spawn")
     a, b = ctx.Pipe(duplex=False)
-    p = ctx.Process(target=_oracle_sample, args=(b, wl_name, n_nodes_full, reps), daemon=True)
-    p.start()
+    saved = {k: os.environ.get(k) for k in BLAS_THREAD_VARS}
+    for k in BLAS_THREAD_VARS:
+        os.environ[k] = "1"
+    try:
+        p = ctx.Process(target=_oracle_sample, args=(b, wl_name, n_nodes_full, reps), daemon=True)
+        p.start()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     return p, a
 
 
