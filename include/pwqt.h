@@ -40,7 +40,10 @@ typedef struct pwqt_ctx pwqt_ctx;
 #define PWQT_ERR_STATE           -5   /* call order violated (e.g. no basis yet)   */
 #define PWQT_ERR_NO_DEVICE       -6   /* no CUDA device / driver                   */
 #define PWQT_ERR_TIMEOUT         -7   /* a bounded wait gave up (device-side wait,
-                                         or pwqt_server_wait before completion)    */
+                                         or pwqt_server_wait before completion);
+                                         if a tensor-core kernel could not drain its
+                                         MMAs it keeps their tensor memory and the
+                                         device is unfit for more tensor-core work */
 #define PWQT_ERR_BUSY            -8   /* the server's request queue is full        */
 
 /* per-result status bits (pwqt_solve `status` output) */
@@ -247,10 +250,15 @@ int pwqt_profile_refinement(pwqt_ctx* ctx, double* residual_ms, double* correcti
  *     (required) and status [n_E] (may be NULL); same meaning as pwqt_solve.
  *   - Requests whose work panels (N n (n+m) complex128 per energy plus n x n
  *     blocks) exceed the 32 MiB return PWQT_ERR_INVALID_ARG and compute nothing.
- *   - The first call on a device looks up the array's device address on that
- *     device (with the device current); make that first call before any stream
- *     capture.  The call enqueues on `stream` (a cudaStream_t, NULL = legacy
- *     default stream) and returns after the stream has finished the work.
+ *   - The first call on a device, even one with n_E = 0, looks up the array's
+ *     device address on that device (with the device current).  Under CUDA's
+ *     lazy module loading that lookup also loads the library's module there and
+ *     commits the 32 MiB, so this first call is the one that can allocate (and
+ *     fail under a quota): make it once at start-up, before any stream capture,
+ *     e.g. with n_E = 0.  Every call makes the context's device current for its
+ *     duration and restores the caller's current device before it returns.  The
+ *     call enqueues on `stream` (a cudaStream_t, NULL = legacy default stream)
+ *     and returns after the stream has finished the work.
  *   - All calls share the array and it keeps the previous call's contents; the
  *     call re-initialises what must start defined.  Calls that overlap on the GPU
  *     (other host threads or streams at the same time) race on it: serialise them.

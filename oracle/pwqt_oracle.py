@@ -43,13 +43,17 @@ reason in the design notes):
     each traveling mode is then refined on the unit circle (Newton on k with
     the band structure of Sec. 5.1 and the Hellmann-Feynman slope), so that
     |lambda| = 1 holds to rounding as Sec. 3.1 states for exact arithmetic.
-  * the 2n modes are sorted into the two sets of n (Sec. 3.1) by an out-flow score:
-    log|lambda| for evanescent modes, -/+1e-5 for traveling modes with dE/dk >/< 0
-    (drain convention); the n lowest scores are the drain's out-flow modes, the n
-    highest the source's.  With a nearly redundant basis (many bands) the pencil
-    is close to singular and spurious eigenvalues can break the lambda <-> 1/lambda*
-    pairing; sorting still yields two sets of size n.  A traveling candidate whose
-    unit-circle refinement does not converge is treated as evanescent.
+  * out-flow modes are classified by the physics of Sec. 3.1: at the drain a mode
+    flows out when |lambda| < 1 (decays into the lead) or when it travels with
+    dE/dk > 0; at the source the mirror image.  Sec. 3.1 fixes N_b = n out-flow
+    and n in-flow modes per contact, so any other count is an error
+    (ModeCountError).  Only on request (allow_sort=True, for diagnosing a nearly
+    redundant basis whose close-to-singular pencil breaks the lambda <-> 1/lambda*
+    pairing) are the 2n modes instead sorted into two sets of n by an out-flow
+    score (log|lambda| for evanescent modes, -/+1e-5 for traveling modes with
+    dE/dk >/< 0); every result built that way carries mode_sorted=True.  A
+    traveling candidate whose unit-circle refinement does not converge is treated
+    as evanescent.
   * degenerate traveling modes are made flux-orthogonal by diagonalising the
     velocity form in the M(lambda) metric.
   * V_e(z) = sum_j U_j f_j(z) (hat interpolation of node potentials); leads
@@ -412,6 +416,11 @@ def lead_modes(blk, Ec: float) -> LeadModes:
     return LeadModes(lam, C, dEdk, trav, Kp, Km, K0, Ec, L, nsets)
 
 
+class ModeCountError(RuntimeError):
+    """The out-flow modes of a contact, classified by Sec. 3.1's physics (decay into
+    the lead, or group velocity pointing out of the device), do not number N_b = n."""
+
+
 @dataclass
 class Contact:
     """Self-energy, Bloch matrix and injection data of one contact (Sec. 3.1-3.2)."""
@@ -425,9 +434,23 @@ class Contact:
     v_in: np.ndarray         # their dE/dk
     rhs: np.ndarray          # n x m injection vectors B_{i,gamma} (Eq. qtbm_system)
     Kprime: np.ndarray
+    mode_sorted: bool = False   # out-flow set chosen by the score sort (allow_sort)
 
 
-def contact(modes: LeadModes, side: str) -> Contact:
+def out_flow_mask(modes: LeadModes, side: str) -> np.ndarray:
+    """Sec. 3.1: the modes leaving the device through this contact.  Drain (lambda =
+    c_{i+1}/c_i): |lambda| < 1 for evanescent modes, dE/dk > 0 for traveling ones.
+    Source (lambda_s = 1/lambda_d): |lambda_d| > 1, or dE/dk < 0."""
+    absl = np.abs(modes.lam)
+    v, trav = modes.dEdk, modes.traveling
+    if side == "d":
+        return np.where(trav, v > 0, absl < 1.0)
+    if side == "s":
+        return np.where(trav, v < 0, absl > 1.0)
+    raise ValueError(side)
+
+
+def contact(modes: LeadModes, side: str, allow_sort: bool = False) -> Contact:
     """Sec. 3.1: Sigma_i = [H'_i - E M'_i] B_i Lambda B_i^-1 from the out-flow modes;
     Sec. 3.2: B_{i,gamma} = [(H'_i - E M'_i) lambda_gamma - Sigma_i] c_gamma for
     each traveling in-flow mode.  Drain: lambda = lambda_d, K' = K_+; out-flow is
@@ -436,21 +459,25 @@ def contact(modes: LeadModes, side: str) -> Contact:
     lam, C, v, trav = modes.lam, modes.C, modes.dEdk, modes.traveling
     absl = np.abs(lam)
     n = C.shape[0]
-    score = np.where(trav, np.where(v > 0, -1e-5, 1e-5), np.log(np.maximum(absl, 1e-300)))
-    order = np.argsort(score, kind="stable")
-    out = np.zeros(2 * n, bool)
+    out = out_flow_mask(modes, side)
+    sorted_ = False
+    if int(out.sum()) != n:
+        if not allow_sort:
+            raise ModeCountError(f"{side}: {int(out.sum())} out-flow modes at Ec = {modes.Ec}, expected n = {n}")
+        # diagnostic fallback: two sets of n by the out-flow score
+        score = np.where(trav, np.where(v > 0, -1e-5, 1e-5), np.log(np.maximum(absl, 1e-300)))
+        order = np.argsort(score, kind="stable")
+        out = np.zeros(2 * n, bool)
+        out[order[:n] if side == "d" else order[n:]] = True
+        sorted_ = True
     if side == "d":
-        out[order[:n]] = True
         inn = trav & ~out & (v < 0)
         lam_c = lam
         Kprime = modes.Kp
-    elif side == "s":
-        out[order[n:]] = True
+    else:
         inn = trav & ~out & (v > 0)
         lam_c = 1.0 / lam
         Kprime = modes.Km
-    else:
-        raise ValueError(side)
     B = C[:, out]
     lo = lam_c[out]
     X = np.linalg.solve(B.T, (B * lo[None, :]).T).T      # B Lambda B^-1
@@ -458,7 +485,7 @@ def contact(modes: LeadModes, side: str) -> Contact:
     cin = C[:, inn]
     lin = lam_c[inn]
     rhs = (Kprime @ cin) * lin[None, :] - Sigma @ cin
-    return Contact(Sigma, B, lo, v[out], trav[out], cin, lin, v[inn], rhs, Kprime)
+    return Contact(Sigma, B, lo, v[out], trav[out], cin, lin, v[inn], rhs, Kprime, sorted_)
 
 
 # =============================================================================
@@ -524,9 +551,10 @@ class EnergyResult:
     src: np.ndarray          # (m_s + m_d,) bool, injected from the source
     n_open_s: int
     n_open_d: int
+    mode_sorted: bool = False   # a contact's modes came from the score-sort fallback
 
 
-def contacts_at(blk, E, Us, Ud, cache=None):
+def contacts_at(blk, E, Us, Ud, cache=None, allow_sort=False):
     """Source and drain contact data at energy E with flat leads at Us and Ud."""
     def modes(Ec):
         if cache is not None and Ec in cache:
@@ -537,15 +565,17 @@ def contacts_at(blk, E, Us, Ud, cache=None):
         return m
     ms = modes(E - Us)
     md = ms if Ud == Us else modes(E - Ud)
-    return contact(ms, "s"), contact(md, "d")
+    return contact(ms, "s", allow_sort), contact(md, "d", allow_sort)
 
 
-def solve_energy(blk, Vd, Vu, U, E, dense_limit=4000, cache=None, contacts=None) -> EnergyResult:
+def solve_energy(blk, Vd, Vu, U, E, dense_limit=4000, cache=None, contacts=None, allow_sort=False) -> EnergyResult:
     """Solve [E M - H - Sigma] c = B (Eq. qtbm_system) for all injected modes at E
-    and reduce to T, R (Eq. transmission) and the node density (Sec. 3.3)."""
+    and reduce to T, R (Eq. transmission) and the node density (Sec. 3.3).
+    Raises ModeCountError when a contact's physical out-flow count is not n, unless
+    allow_sort (then the result carries mode_sorted=True)."""
     N, n = Vd.shape[0], blk["n"]
     Us, Ud = float(U[0]), float(U[-1])
-    cs, cd = contacts if contacts is not None else contacts_at(blk, E, Us, Ud, cache)
+    cs, cd = contacts if contacts is not None else contacts_at(blk, E, Us, Ud, cache, allow_sort)
     ms, md = cs.c_in.shape[1], cd.c_in.shape[1]
     m = ms + md
     rhs = np.zeros((N * n, m), complex)
@@ -588,7 +618,7 @@ def observables(E, c, cs: Contact, cd: Contact, ms: int, md: int) -> EnergyResul
     w = (np.abs(c) ** 2).sum(axis=1)                     # (N, m)
     node_n = np.stack([(w[:, :ms] * g[None, :ms]).sum(1), (w[:, ms:] * g[None, ms:]).sum(1)], 1)
     return EnergyResult(E, float(Tm.sum()), float(Rm.sum()), Tm, Rm, T_ds, node_n, c, g, src,
-                        ms, md)
+                        ms, md, bool(cs.mode_sorted or cd.mode_sorted))
 
 
 # =============================================================================

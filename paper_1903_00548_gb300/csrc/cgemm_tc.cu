@@ -204,9 +204,12 @@ k_cgemm_tc(const CGemmArgs G, int M, int N, int K) {
         }
         __syncthreads();
     }
+    bool drained = true;   // no MMA of this CTA can still write its tensor memory
     if (!ok) {
         if (tid == 0) atomicExch(&g_tc_error, 1);
-        mbar_wait(smem_u32(mbar), phase ^ 1u);   // bounded second wait for the MMAs in flight
+        // bounded second wait for the MMAs in flight (the phase that timed out); the
+        // block agrees on the outcome before anyone decides about the dealloc
+        drained = __syncthreads_and(mbar_wait(smem_u32(mbar), phase ^ 1u)) != 0;
     } else {
         // ---- epilogue: C -= acc.  A thread holds one tile row ((warp % 4) * 32 + lane) and 128
         // real columns; the tile goes through shared memory (rows padded to an odd stride, so
@@ -231,7 +234,15 @@ k_cgemm_tc(const CGemmArgs G, int M, int N, int K) {
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TMEM_COLS));
+    // Tensor memory that an outstanding MMA may still write is not handed back: a
+    // later CTA could be given it while the write lands.  The kernel reports error
+    // code 2 instead and the host returns PWQT_ERR_TIMEOUT (the device is then not
+    // fit for further tensor-core work in this process).
+    if (drained) {
+        if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TMEM_COLS));
+    } else if (tid == 0) {
+        atomicExch(&g_tc_error, 2);
+    }
 }
 }  // namespace
 

@@ -14,7 +14,8 @@
 //     inverse iteration for c converge to |lambda| = 1 exactly.
 //  3. Traveling modes are normalised to c^H M(lambda) c = L/2pi (Eq. normalization).
 //  4. Out-flow modes form the Bloch matrices B_d (|lambda| < 1 or dE/dk > 0) and
-//     B_s (|lambda_d| > 1 or dE/dk < 0, lambda_s = 1/lambda_d); Sigma = K' B Lambda B^-1
+//     B_s (|lambda_d| > 1 or dE/dk < 0, lambda_s = 1/lambda_d), n columns each (any
+//     other count: PWQT_ST_MODE_COUNT, energy not solved); Sigma = K' B Lambda B^-1
 //     with K'_d = K+, K'_s = K-; injection vectors B_gamma = (K' lambda_gamma - Sigma) c_gamma.
 #include <algorithm>
 #include <atomic>
@@ -339,26 +340,20 @@ int compute_lead_shared(const pwqt_ctx* bz, pwqt_ctx* c, const LeadWorker& wk, d
                 }
             }
 
-    // ---- classification (drain convention lambda = c_{i+1}/c_i): sort the 2n modes into
-    // two sets of n by an out-flow score, log|lambda| for evanescent modes and -/+1e-5 for
-    // traveling modes with dE/dk >/< 0; the n lowest are the drain's out-flow modes, the
-    // n highest the source's (a nearly redundant basis makes the pencil close to singular,
-    // so spurious eigenvalues need not pair lambda <-> 1/lambda^*).
-    std::vector<double> score(n2);
-    for (int j = 0; j < n2; ++j)
-        score[j] = trav[j] ? (dEdk[j] > 0 ? -1e-5 : 1e-5) : std::log(std::max(std::hypot(hlam[j].x, hlam[j].y), 1e-300));
-    std::vector<int> order(n2);
-    for (int j = 0; j < n2; ++j) order[j] = j;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return score[a] < score[b]; });
-    std::vector<char> is_out_d(n2, 0), is_out_s(n2, 0);
-    for (int q = 0; q < n; ++q) is_out_d[order[q]] = 1;
-    for (int q = n; q < n2; ++q) is_out_s[order[q]] = 1;
+    // ---- classification (Sec. 3.1, drain convention lambda = c_{i+1}/c_i): a mode leaves
+    // through the drain when it decays into it (|lambda| < 1) or travels with dE/dk > 0,
+    // through the source when |lambda| > 1 or dE/dk < 0.  The section fixes n out-flow
+    // modes per contact; any other count marks the energy PWQT_ST_MODE_COUNT and it is
+    // not solved.
     std::vector<int> out_d, in_d, out_s, in_s;
     for (int j = 0; j < n2; ++j) {
-        if (is_out_d[j]) out_d.push_back(j);
-        else if (trav[j] && dEdk[j] < 0) in_d.push_back(j);
-        if (is_out_s[j]) out_s.push_back(j);
-        else if (trav[j] && dEdk[j] > 0) in_s.push_back(j);
+        const double al = std::hypot(hlam[j].x, hlam[j].y);
+        const bool od = trav[j] ? dEdk[j] > 0 : al < 1.0;
+        const bool os = trav[j] ? dEdk[j] < 0 : al > 1.0;
+        if (od) out_d.push_back(j);
+        if (os) out_s.push_back(j);
+        if (trav[j] && dEdk[j] < 0) in_d.push_back(j);
+        if (trav[j] && dEdk[j] > 0) in_s.push_back(j);
     }
     auto E = std::make_unique<LeadEntry>();
     E->Ec = Ec;

@@ -6,6 +6,7 @@
 // fragmentation).  Its work panels and job tables live in the file-scope array
 // below; inputs (the context's assembled system and cached self-energies) and
 // outputs (caller-owned device buffers) are the caller's.
+#include <atomic>
 #include <cmath>
 
 #include "pwqt_internal.cuh"
@@ -20,9 +21,24 @@ constexpr int NOALLOC_MAX_ENERGIES = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 // device address of g_noalloc_scratch per device ordinal, set up on the first call
-static void* g_noalloc_base[128] = {nullptr};
+static std::atomic<void*> g_noalloc_base[128];
 
 static size_t up256(size_t b) { return (b + 255) / 256 * 256; }
+
+// makes the context's device current for the call and gives the caller's current
+// device back on every return path
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev) {
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
 
 }  // namespace pwqt
 
@@ -36,21 +52,24 @@ extern "C" int pwqt_solve_noalloc(pwqt_ctx* c, int sys, int n_E, const double* E
     if (it == c->systems.end()) return fail(c, PWQT_ERR_STATE, "unknown system: call pwqt_set_extrinsic first");
     if (n_E < 0 || n_E > NOALLOC_MAX_ENERGIES || (n_E > 0 && !E))
         return fail(c, PWQT_ERR_INVALID_ARG, "pwqt_solve_noalloc takes 0.." + std::to_string(NOALLOC_MAX_ENERGIES) + " energies");
-    if (n_E == 0) return PWQT_OK;
-    if (!T || !R || !T_ds || !node_n) return fail(c, PWQT_ERR_INVALID_ARG, "T, R, T_ds and node_n device buffers are required");
     if (c->dev < 0 || c->dev >= 128) return fail(c, PWQT_ERR_INVALID_ARG, "device ordinal out of range");
-    for (int e = 0; e < n_E; ++e)
-        if (!std::isfinite(E[e])) return fail(c, PWQT_ERR_INVALID_ARG, "non-finite energy");
-    PWQT_CUDA(c, cudaSetDevice(c->dev));
-    // one-time set-up on this device (with the device current): the host-side name of
-    // the array is only a stand-in, the kernels need its device address
-    if (!g_noalloc_base[c->dev]) {
+    DeviceGuard guard(c->dev);
+    if (guard.err != cudaSuccess) return cuda_fail(c, guard.err, "cudaSetDevice");
+    // one-time set-up on this device (with the device current), done by the first call
+    // even when it has no energies: the host-side name of the array is only a stand-in,
+    // the kernels need its device address.  With lazy module loading this lookup is
+    // also what loads the library's module on the device and commits the array there.
+    if (!g_noalloc_base[c->dev].load()) {
         void* ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess || !ptr) return cuda_fail(c, e == cudaSuccess ? cudaErrorInvalidSymbol : e, "cudaGetSymbolAddress(scratch)");
-        g_noalloc_base[c->dev] = ptr;
+        g_noalloc_base[c->dev].store(ptr);
     }
-    char* base = static_cast<char*>(g_noalloc_base[c->dev]);
+    if (n_E == 0) return PWQT_OK;
+    if (!T || !R || !T_ds || !node_n) return fail(c, PWQT_ERR_INVALID_ARG, "T, R, T_ds and node_n device buffers are required");
+    for (int e = 0; e < n_E; ++e)
+        if (!std::isfinite(E[e])) return fail(c, PWQT_ERR_INVALID_ARG, "non-finite energy");
+    char* base = static_cast<char*>(g_noalloc_base[c->dev].load());
     System& s = it->second;
     const int n = c->n, N = s.N;
     const size_t nn = (size_t)n * n;

@@ -5,11 +5,11 @@ as the bench does, at two energies of the bench's grid.  The expected values wer
 written by tests/golden/make_block512.py, which calls only the oracle (its lead
 eigenproblems take minutes at this block size, too long to run here).
 
-Tolerances as in the transmission parity tests: T, R, T_ds within tol * max(1,
-open channels), or four times the sum of both sides' reciprocity defects where that
-is larger; tol = 1e-9 for the FP64 path and 1e-8 for the mixed path with its
-default stopping rule (the 1e-8 bar on T); node densities (coefficient space, see
-the parity tests) within 1e-7 of their largest value; open-channel counts exact."""
+Tolerances as in the transmission parity tests: FP64 path, T, R, T_ds within 1e-9
+relative (times max(1, open channels)); mixed path with its default stopping rule,
+1e-8 absolute (the bar on T); either widened only to four times the oracle's own
+reciprocity defect where that is larger; node densities (coefficient space, see the
+parity tests) within 1e-7 of their largest value; open-channel counts exact."""
 import json
 import os
 
@@ -50,8 +50,8 @@ def test_block512_matches_oracle(pw, solved, prec, tol):
     assert np.all(r.status & bad == 0), r.status
     for e, ref in enumerate(g["energies"]):
         assert tuple(r.n_open[e]) == tuple(ref["n_open"]), e
-        scale = max(1.0, ref["n_open"][0])
-        t = max(tol * scale, 4.0 * (ref["defect"] + abs(r.T[e] - r.T_ds[e])))
+        scale = max(1.0, ref["n_open"][0]) if prec == "FP64" else 1.0
+        t = max(tol * scale, 4.0 * ref["defect"])
         for key, got in (("T", r.T[e]), ("R", r.R[e]), ("T_ds", r.T_ds[e])):
             assert abs(got - ref[key]) <= t, (prec, ref["E"], key, got, ref[key], t)
         nn = np.array(ref["node_n"])

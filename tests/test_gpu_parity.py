@@ -1,9 +1,11 @@
 """CUDA path (through the C ABI) against the oracle, element by element on the
 same seeded inputs.
 
-Tolerances (FP64 path): 1e-9 relative on T, R and T_ds, or four times the sum of
-the two sides' own measured errors at that energy where that is larger (each
-side's reciprocity defect |T - T_ds|, zero in exact arithmetic); blocks and bands 1e-11 / 1e-10 relative.  The node density sum_alpha |c_i alpha|^2 is a coefficient-space
+Tolerances (FP64 path): 1e-9 relative on T, R and T_ds (relative to the number of
+open channels, which bounds them), or four times the oracle's own error bar at that
+energy where that is larger (its reciprocity defect |T - T_ds|, zero in exact
+arithmetic; the GPU's own defect never widens the bound); mixed path: 1e-8
+absolute on the same terms; blocks and bands 1e-11 / 1e-10 relative.  The node density sum_alpha |c_i alpha|^2 is a coefficient-space
 sum: the PU Bloch basis is nearly linearly dependent (M(k) has eigenvalues ~1e-6
 of its largest, kappa(A) ~ 4e6 measured on these systems), so components of c along
 those near-null directions carry kappa * u_64 ~ 1e-9 rounding in both the oracle
@@ -54,13 +56,12 @@ def oracle_error(r):
     return abs(r.T - r.T_ds)
 
 
-def _compare(res_gpu, res_or, tol=TOL):
+def _compare(res_gpu, res_or, tol=TOL, absolute=False):
     for e, r in enumerate(res_or):
         assert tuple(res_gpu.n_open[e]) == (r.n_open_s, r.n_open_d), e
-        scale = max(1.0, r.n_open_s)
-        # each side's exact-reciprocity defect estimates its own rounding error
-        gpu_err = abs(res_gpu.T[e] - res_gpu.T_ds[e])
-        t = max(tol * scale, 4.0 * (oracle_error(r) + gpu_err))
+        scale = 1.0 if absolute else max(1.0, r.n_open_s)
+        # the oracle's exact-reciprocity defect is its own error bar at this energy
+        t = max(tol * scale, 4.0 * oracle_error(r))
         assert abs(res_gpu.T[e] - r.T) <= t, (e, res_gpu.T[e], r.T, t)
         assert abs(res_gpu.R[e] - r.R) <= t, (e, res_gpu.R[e], r.R, t)
         assert abs(res_gpu.T_ds[e] - r.T_ds) <= t, (e, res_gpu.T_ds[e], r.T_ds, t)
@@ -198,24 +199,25 @@ def test_cache_reuse_gives_identical_results(pw, chain):
 
 
 def test_chain_parity_statistics(pw, chain):
-    # most energies meet the plain 1e-9 bar; report how many need the oracle's error bar
+    # every energy meets the plain 1e-9 bar or the oracle's own error bar there
+    # (4 |T - T_ds| of the oracle); report how many needed the latter
     wl, s = chain
     ctx = _ctx_with_basis(pw, s)
     ctx.set_extrinsic(0, wl.U)
     res = ctx.solve(0, wl.energies, pw.FP64)
     ref = _oracle_results(s, wl.energies)
     d = np.array([abs(res.T[e] - r.T) for e, r in enumerate(ref)])
+    bar = np.array([4.0 * oracle_error(r) for r in ref])
     within = np.mean(d <= 1e-9)
     print(f"T parity: max |dT| = {d.max():.2e}, {100 * within:.0f}% of energies within 1e-9")
-    assert within >= 0.75
-    assert d.max() < 1e-7
+    assert np.all(d <= np.maximum(1e-9, bar)), (d.max(), np.argmax(d - np.maximum(1e-9, bar)))
 
 
 # ---------------------------------------------------------------- mixed precision
-# complex64 factorisation on the tensor cores (3xTF32) + refinement with
-# float-float residuals: T within 1e-8 of the oracle (or 4x the two sides'
-# reciprocity defects).  The small systems below refine to 1e-11 (tighter than the
-# 1e-9 default) so that the refinement loop itself is checked well past the bar.
+# complex64 factorisation on the tensor cores (3xTF32) + refinement: T within 1e-8
+# absolute of the oracle (or 4x the oracle's reciprocity defect).  The small systems
+# below refine to 1e-11 so that the refinement loop itself is checked well past the
+# bar.
 MIXED_TOL = 1e-8
 
 
@@ -226,7 +228,7 @@ def test_mixed_chain_all_energies(pw, chain):
     ctx.set_extrinsic(0, wl.U)
     res = ctx.solve(0, wl.energies, pw.MIXED)
     ref = _oracle_results(s, wl.energies)
-    _compare(res, ref, tol=MIXED_TOL)
+    _compare(res, ref, tol=MIXED_TOL, absolute=True)
     open_e = res.n_open.sum(1) > 0
     assert np.all(res.iters[open_e] >= 1)
     assert np.max(res.resid) <= 1e-10
@@ -241,7 +243,7 @@ def test_mixed_small_ribbon(pw):
     ctx.set_extrinsic(0, s.U)
     Es = np.array([0.25, 0.6, 1.1, 1.7, 2.3])
     res = ctx.solve(0, Es, pw.MIXED)
-    _compare(res, _oracle_results(s, Es), tol=MIXED_TOL)
+    _compare(res, _oracle_results(s, Es), tol=MIXED_TOL, absolute=True)
     assert np.max(res.resid) <= 1e-10
 
 
@@ -253,10 +255,11 @@ def test_mixed_matches_fp64_path_on_a_longer_ribbon(pw):
     ctx.set_extrinsic(0, s.U)
     Es = np.array([0.4, 1.3, 2.1])
     r64 = ctx.solve(0, Es, pw.FP64)
-    rmx = ctx.solve(0, Es, pw.MIXED)   # default stopping rule (residual 1e-9)
+    rmx = ctx.solve(0, Es, pw.MIXED)   # default stopping rule
     assert np.all(rmx.resid <= 1e-8)
-    t = np.maximum(MIXED_TOL * np.maximum(1, r64.n_open[:, 0]), 4 * np.abs(r64.T - r64.T_ds))
-    assert np.all(np.abs(rmx.T - r64.T) <= t + 4 * np.abs(rmx.T - rmx.T_ds))
+    ref = _oracle_results(s, Es)
+    _compare(rmx, ref, tol=MIXED_TOL, absolute=True)
+    assert np.all(np.abs(rmx.T - r64.T) <= MIXED_TOL)
     assert np.all(rmx.status & ~pw.ST_NEAR_UNIT == 0)
 
 
@@ -308,9 +311,11 @@ def test_caroli_transmission_cross_check(pw, chain):
         ctx.set_extrinsic(0, sys_.U)
         Tc, st = ctx.transmission_caroli(0, Es)
         res = ctx.solve(0, Es, pw.FP64)
+        cache = {}
         for e, E in enumerate(Es):
-            ref = O.caroli_transmission(sys_.blk, sys_.Vd, sys_.Vu, sys_.U, float(E))
-            t = 1e-9 * max(1.0, ref) + 4 * abs(res.T[e] - res.T_ds[e])
+            ref = O.caroli_transmission(sys_.blk, sys_.Vd, sys_.Vu, sys_.U, float(E), cache=cache)
+            bar = oracle_error(O.solve_energy(sys_.blk, sys_.Vd, sys_.Vu, sys_.U, float(E), cache=cache))
+            t = max(1e-9 * max(1.0, ref), 4 * bar)
             assert abs(Tc[e] - ref) <= t, (E, Tc[e], ref)
             assert abs(Tc[e] - res.T[e]) <= t, (E, Tc[e], res.T[e])
         assert np.all(st & pw.ST_MODE_COUNT == 0)

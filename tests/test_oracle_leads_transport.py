@@ -80,8 +80,15 @@ def test_lead_modes_invariants(which):
             c, lam = lm.C[:, j], lm.lam[j]
             r = (lm.Km / lam + lm.K0 + lam * lm.Kp) @ c
             assert np.linalg.norm(r) < 1e-8 * max(1.0, abs(lam), 1 / abs(lam)) * np.linalg.norm(lm.K0)
+        # Sec. 3.1: exactly n out-flow modes per contact, from the physics alone
+        # (decay into the lead or velocity out of the device), and every traveling
+        # mode leaves through exactly one contact
+        od, os_ = O.out_flow_mask(lm, "d"), O.out_flow_mask(lm, "s")
+        assert od.sum() == n and os_.sum() == n
+        assert not np.any(od & os_) and np.all(od | os_)
         cd = O.contact(lm, "d")
         cs = O.contact(lm, "s")
+        assert not cd.mode_sorted and not cs.mode_sorted
         # X = B Lambda B^-1 solves the matrix quadratic of the semi-infinite lead
         Xd = cd.B @ np.diag(cd.lam_out) @ np.linalg.inv(cd.B)
         Xs = cs.B @ np.diag(cs.lam_out) @ np.linalg.inv(cs.B)

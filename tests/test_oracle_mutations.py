@@ -40,8 +40,8 @@ def test_unmutated_pins_hold():
 def _mutated_contact(kind):
     orig = O.contact
 
-    def bad(modes, side):
-        c = orig(modes, side)
+    def bad(modes, side, allow_sort=False):
+        c = orig(modes, side, allow_sort)
         if kind == "sigma_sign":
             c.Sigma = -c.Sigma
         elif kind == "bloch_transpose":
@@ -126,3 +126,36 @@ def test_wrong_mode_normalisation_is_caught(monkeypatch):
     monkeypatch.setattr(O, "lead_modes", bad)
     r = O.solve_energy(s.blk, s.Vd, s.Vu, s.U, 0.4)
     assert abs(r.T + r.R - 1.0) > 1e-4
+
+
+def test_flipped_traveling_velocity_breaks_the_mode_count(monkeypatch):
+    # Sec. 3.1: n out-flow and n in-flow modes per contact.  One traveling mode with
+    # the wrong flow direction leaves n + 1 (or n - 1) out-flow modes: the oracle
+    # must report it, not absorb it.
+    wl = W.chain8()
+    s = O.build_system(wl.cell, W.FormFactor(), wl.gcut, wl.n_bands, wl.U)
+    O.solve_energy(s.blk, s.Vd, s.Vu, s.U, 0.4)          # unmutated: count is n
+    orig = O.lead_modes
+
+    def flipped_one(blk, Ec):
+        m = orig(blk, Ec)
+        j = int(np.flatnonzero(m.traveling)[0])
+        m.dEdk = m.dEdk.copy()
+        m.dEdk[j] = -m.dEdk[j]
+        return m
+    monkeypatch.setattr(O, "lead_modes", flipped_one)
+    with pytest.raises(O.ModeCountError):
+        O.solve_energy(s.blk, s.Vd, s.Vu, s.U, 0.4)
+    # the diagnostic score sort still returns a result, flagged
+    r = O.solve_energy(s.blk, s.Vd, s.Vu, s.U, 0.4, allow_sort=True)
+    assert r.mode_sorted
+
+
+def test_jacobian_factor_mistake_is_caught(monkeypatch):
+    # Eq. density_jacobian: the weight -f' of the Jacobian; a factor-of-two slip must
+    # fail the finite-difference pin of tests/test_oracle_selfconsistent.py
+    from tests.test_oracle_selfconsistent import jacobian_matches_mu_derivative
+    assert jacobian_matches_mu_derivative()
+    orig = O.dfermi
+    monkeypatch.setattr(O, "dfermi", lambda x, kT: 0.5 * orig(x, kT))
+    assert not jacobian_matches_mu_derivative()

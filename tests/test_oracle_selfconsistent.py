@@ -1,5 +1,7 @@
 """Pins of the oracle's self-consistent loop (Sec. 4: non-linear Poisson by Newton with
 the semi-classical Jacobian, DIIS acceleration) on a 1D finite-element model."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -59,3 +61,39 @@ def test_newton_and_diis_reach_the_same_self_consistent_potential(setup):
     # (on this 1.6 nm-wide gate the quantum response of the node density is far weaker
     # than the semi-classical estimate that the Jacobian uses, so no sign of the screening
     # is asserted: that the loop converges anyway is the point of the approximation)
+
+
+def test_fermi_derivative_is_the_derivative_of_fermi():
+    # -df/dE by central differences of the Fermi function itself (h^2 f'''/6 ~ 1e-7)
+    x = np.linspace(-0.3, 0.3, 61)
+    h = 2e-5
+    fd = -(O.fermi(x + h, KT) - O.fermi(x - h, KT)) / (2 * h)
+    assert np.max(np.abs(O.dfermi(x, KT) - fd)) < 1e-6 * np.max(fd)
+    # normalisation: int -f' dE = 1
+    xs = np.linspace(-1.0, 1.0, 20001)
+    assert abs(np.trapezoid(O.dfermi(xs, KT), xs) - 1.0) < 1e-9
+
+
+@functools.lru_cache(maxsize=None)
+def _pristine_chain():
+    return with_potential(chain_system(), np.zeros(20)), {}
+
+
+def jacobian_matches_mu_derivative(mu=MU, h=4e-3, tol=1e-6):
+    """Eq. density_jacobian: with both contacts at mu, the Jacobian diagonal that
+    density_and_jacobian returns, d_i = int n_i(E) (-f'(E - mu)) dE / L, is the
+    derivative in mu of the node density it returns, n_i(mu) = int n_i(E) f(E - mu)
+    dE / L.  The derivative by central differences of density_and_jacobian itself at
+    mu +- h on a fixed energy window, integrated to a tolerance far below the
+    difference it resolves."""
+    s, cache = _pristine_chain()
+    hi = mu + 14 * KT
+    n_p, _, _ = O.density_and_jacobian(s, mu + h, mu + h, KT, E_LO, hi, tol, cache)
+    n_m, _, _ = O.density_and_jacobian(s, mu - h, mu - h, KT, E_LO, hi, tol, cache)
+    _, d, _ = O.density_and_jacobian(s, mu, mu, KT, E_LO, hi, tol, cache)
+    fd = (n_p - n_m) / (2 * h)
+    return bool(np.max(np.abs(d - fd)) <= 2e-3 * np.max(np.abs(fd)))
+
+
+def test_jacobian_is_the_mu_derivative_of_the_density():
+    assert jacobian_matches_mu_derivative()

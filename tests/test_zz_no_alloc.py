@@ -50,6 +50,30 @@ def test_noalloc_matches_allocating_solve_twice(setup):
         assert np.array_equal(got["status"], ref.status)
 
 
+def test_noalloc_matches_oracle(setup):
+    # the same energies through the oracle: 1e-9 relative (times the open channels),
+    # or four times the oracle's own reciprocity defect where that is larger
+    from oracle import pwqt_oracle as O
+    torch, pwqt, wl, ctx = setup
+    E = wl.energies[40:48]
+    ctx.solve(0, E, pwqt.FP64)                                  # fills the self-energy cache
+    got = _run_noalloc(torch, ctx, E, wl.n_nodes)
+    s = O.build_system(wl.cell, wl.ff, wl.gcut, wl.n_bands, wl.U)
+    cache = {}
+    for e, En in enumerate(E):
+        r = O.solve_energy(s.blk, s.Vd, s.Vu, s.U, float(En), cache=cache)
+        t = max(TOL * max(1.0, r.n_open_s), 4.0 * abs(r.T - r.T_ds))
+        assert abs(got["T"][e] - r.T) <= t and abs(got["R"][e] - r.R) <= t, (En, got["T"][e], r.T)
+
+
+def test_noalloc_empty_call_and_device_restore(setup):
+    # an empty call does the one-time set-up; the caller's current device is kept
+    torch, pwqt, wl, ctx = setup
+    before = torch.cuda.current_device()
+    ctx.solve_noalloc(0, np.zeros(0), {})
+    assert torch.cuda.current_device() == before
+
+
 def test_noalloc_rejects_what_it_cannot_do(setup):
     torch, pwqt, wl, ctx = setup
     # energies whose self-energies are not cached: it would have to allocate
