@@ -58,7 +58,8 @@ typedef struct pwqt_ctx pwqt_ctx;
 #define PWQT_FP64                0    /* complex128 throughout                     */
 #define PWQT_MIXED               1    /* complex64 factorisation on the tensor
                                          cores (3xTF32 products, FP32 accumulate)
-                                         + refinement with float-float residuals   */
+                                         + refinement with FP64-accurate residuals
+                                         (see pwqt_set_residual)                   */
 #define PWQT_FP32                2    /* the complex64 factorisation alone (no
                                          refinement; resid reports its residual)   */
 
@@ -66,8 +67,9 @@ typedef struct {
     int    device;             /* CUDA device ordinal                              */
     size_t hbm_budget_bytes;   /* 0: use 90 % of the free device memory            */
     double ir_tol;             /* mixed path: stop when ||B - A c|| <= ir_tol ||B||
-                                  (max over columns), or when the residual stalls
-                                  within 10 ir_tol; 0 -> 1e-9                       */
+                                  (max over columns); 0 -> 1e-10.  A residual that
+                                  stops falling above it ends the refinement with
+                                  PWQT_ST_IR_NO_CONVERGE                            */
     int    ir_max_iters;       /* mixed path refinement limit; 0 -> 40              */
     int    batch;              /* energies per sweep launch; 0 -> from the budget   */
 } pwqt_opts;
@@ -233,6 +235,22 @@ int pwqt_set_refinement(pwqt_ctx* ctx, double ir_tol, int ir_max_iters);
  * pointer may be NULL.
  */
 int pwqt_profile_refinement(pwqt_ctx* ctx, double* residual_ms, double* correction_ms, long long* iterations);
+
+/*
+ * Refinement residual of the mixed path (Sec. 3.2 system, r = B - A c; the paper
+ * solves in FP64 directly and has no counterpart):
+ *   PWQT_RESIDUAL_SLICED (default): FP64-accurate products on the bf16 tensor
+ *     cores -- operands cut into 7-bit integer slices whose products the tensor
+ *     cores sum exactly; residual error ~3e-12 ||B|| on the block-512 workload.
+ *     Its slice panels take (N + 1) x 44 MB per system at n = 512 (built on the
+ *     first mixed solve of a system, kept with it).
+ *   PWQT_RESIDUAL_FLOAT_FLOAT: float-float arithmetic on the FP32 pipes
+ *     (~48-bit significand; floor ~4e-10 ||B|| at block 512).
+ * Errors: PWQT_ERR_INVALID_ARG for any other value.
+ */
+#define PWQT_RESIDUAL_SLICED       0
+#define PWQT_RESIDUAL_FLOAT_FLOAT  1
+int pwqt_set_residual(pwqt_ctx* ctx, int kind);
 
 /*
  * pwqt_solve_noalloc -- the FP64 solve without any device allocation.

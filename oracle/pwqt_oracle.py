@@ -362,13 +362,16 @@ def refine_traveling(blk, Ec: float, lam, c, iters: int = 8):
     return False, best[0], best[1]
 
 
-def lead_modes(blk, Ec: float) -> LeadModes:
+def lead_modes(blk, Ec: float, reciprocal: bool = False) -> LeadModes:
     """Complex band structure at energy Ec of the flat lead (Eqs. complex_bs and
     linearized_eigenvalue_symmetric): the 2n x 2n pencil
         [[K0, K-], [K+, 0]] [d; c] = lambda [[-K+, 0], [0, K+]] [d; c],  d = lambda c,
     K(E) = H - E M, solved by generalised QZ.  Traveling modes get their
     Hellmann-Feynman velocity (Eq. hellmann-feynman) and the normalisation
-    c^H M(lambda) c = L/2pi (Eq. normalization); evanescent modes unit norm."""
+    c^H M(lambda) c = L/2pi (Eq. normalization); evanescent modes unit norm.
+    reciprocal=True solves the same pencil for mu = 1/lambda (QZ of (B, A)): the
+    same modes by a different rounding path, so that the spread of the results
+    measures the oracle's own rounding error."""
     n, L = blk["n"], blk["L"]
     K0 = blk["H0"] - Ec * blk["M0"]
     Kp = blk["H1"] - Ec * blk["M1"]
@@ -376,7 +379,12 @@ def lead_modes(blk, Ec: float) -> LeadModes:
     Z = np.zeros((n, n), complex)
     A = np.block([[K0, Km], [Kp, Z]])
     B = np.block([[-Kp, Z], [Z, Kp]])
-    lam, V = sla.eig(A, B)
+    if reciprocal:
+        mu, V = sla.eig(B, A)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            lam = np.where(mu == 0, np.inf, 1.0 / mu)
+    else:
+        lam, V = sla.eig(A, B)
     C = V[n:, :].copy()
     C /= np.linalg.norm(C, axis=0)[None, :]
     absl = np.abs(lam)
@@ -554,28 +562,31 @@ class EnergyResult:
     mode_sorted: bool = False   # a contact's modes came from the score-sort fallback
 
 
-def contacts_at(blk, E, Us, Ud, cache=None, allow_sort=False):
+def contacts_at(blk, E, Us, Ud, cache=None, allow_sort=False, reciprocal=False):
     """Source and drain contact data at energy E with flat leads at Us and Ud."""
     def modes(Ec):
-        if cache is not None and Ec in cache:
-            return cache[Ec]
-        m = lead_modes(blk, Ec)
+        key = ("reciprocal", Ec) if reciprocal else Ec
+        if cache is not None and key in cache:
+            return cache[key]
+        m = lead_modes(blk, Ec, reciprocal)
         if cache is not None:
-            cache[Ec] = m
+            cache[key] = m
         return m
     ms = modes(E - Us)
     md = ms if Ud == Us else modes(E - Ud)
     return contact(ms, "s", allow_sort), contact(md, "d", allow_sort)
 
 
-def solve_energy(blk, Vd, Vu, U, E, dense_limit=4000, cache=None, contacts=None, allow_sort=False) -> EnergyResult:
+def solve_energy(blk, Vd, Vu, U, E, dense_limit=4000, cache=None, contacts=None, allow_sort=False,
+                 reciprocal=False) -> EnergyResult:
     """Solve [E M - H - Sigma] c = B (Eq. qtbm_system) for all injected modes at E
     and reduce to T, R (Eq. transmission) and the node density (Sec. 3.3).
     Raises ModeCountError when a contact's physical out-flow count is not n, unless
-    allow_sort (then the result carries mode_sorted=True)."""
+    allow_sort (then the result carries mode_sorted=True).  reciprocal: lead modes
+    from the reciprocal pencil (see lead_modes)."""
     N, n = Vd.shape[0], blk["n"]
     Us, Ud = float(U[0]), float(U[-1])
-    cs, cd = contacts if contacts is not None else contacts_at(blk, E, Us, Ud, cache, allow_sort)
+    cs, cd = contacts if contacts is not None else contacts_at(blk, E, Us, Ud, cache, allow_sort, reciprocal)
     ms, md = cs.c_in.shape[1], cd.c_in.shape[1]
     m = ms + md
     rhs = np.zeros((N * n, m), complex)
@@ -642,6 +653,13 @@ def build_system(cell, ff, gcut, n_bands, U, nq=None, basis=None) -> System:
     blk = intrinsic_blocks(elem)
     Vd, Vu = extrinsic_blocks(blk, U)
     return System(basis, elem, blk, np.asarray(U, float), Vd, Vu)
+
+
+def error_bar(r: EnergyResult, r_alt: EnergyResult) -> float:
+    """The oracle's own rounding error at one energy, from what exact arithmetic
+    fixes: total transmission is reciprocal (T_sd = T_ds for a real potential), and
+    the same modes from the reciprocal pencil give the same T, R, T_ds."""
+    return max(abs(r.T - r.T_ds), abs(r.T - r_alt.T), abs(r.T_ds - r_alt.T_ds), abs(r.R - r_alt.R))
 
 
 def solve_workload(sys_: System, energies, cache=None):

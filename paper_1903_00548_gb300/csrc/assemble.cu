@@ -383,6 +383,8 @@ int assemble_from_basis(pwqt_ctx* c, const pwqt_cell* cell, int n_bands, const d
     PWQT_CUDA(c, cudaGetLastError());
     PWQT_TRY(alloc(c, c->H0, sizeof(double2) * nn));
     PWQT_TRY(alloc(c, c->H1, sizeof(double2) * nn));
+    c->ozM.release();          // slice panels of the previous basis
+    c->ozM_rexp.release();
     PWQT_TRY(alloc(c, c->M0, sizeof(double2) * nn));
     PWQT_TRY(alloc(c, c->M1, sizeof(double2) * nn));
     PWQT_TRY(alloc(c, c->W, sizeof(double2) * nn * 6));
@@ -443,6 +445,8 @@ __global__ void k_system_blocks(int n, int N, const double* __restrict__ U, cons
 }
 
 int build_system_blocks(pwqt_ctx* c, System& s) {
+    s.ozH.release();           // slice panels of the previous potential
+    s.ozH_rexp.release();
     int n = c->n, N = s.N;
     size_t nn = (size_t)n * n;
     DBuf dU;

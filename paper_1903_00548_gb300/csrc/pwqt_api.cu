@@ -44,7 +44,7 @@ int pwqt_create(pwqt_ctx** out, const pwqt_opts* opts) {
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) { cudaGetLastError(); return PWQT_ERR_NO_DEVICE; }
     auto* c = new pwqt_ctx();
     if (opts) c->opts = *opts;
-    if (c->opts.ir_tol <= 0) c->opts.ir_tol = 1e-9;
+    if (c->opts.ir_tol <= 0) c->opts.ir_tol = 1e-10;
     if (c->opts.ir_max_iters <= 0) c->opts.ir_max_iters = 40;
     c->dev = c->opts.device;
     if (c->dev < 0 || c->dev >= ndev) { delete c; return PWQT_ERR_INVALID_ARG; }
@@ -373,8 +373,16 @@ int pwqt_set_refinement(pwqt_ctx* c, double ir_tol, int ir_max_iters) {
     PWQT_TRY(check_ctx(c));
     if (!(ir_tol >= 0) || !std::isfinite(ir_tol) || ir_max_iters < 0)
         return fail(c, PWQT_ERR_INVALID_ARG, "ir_tol must be finite and >= 0, ir_max_iters >= 0");
-    c->opts.ir_tol = ir_tol > 0 ? ir_tol : 1e-9;
+    c->opts.ir_tol = ir_tol > 0 ? ir_tol : 1e-10;
     c->opts.ir_max_iters = ir_max_iters > 0 ? ir_max_iters : 40;
+    return PWQT_OK;
+}
+
+int pwqt_set_residual(pwqt_ctx* c, int kind) {
+    PWQT_TRY(check_ctx(c));
+    if (kind != PWQT_RESIDUAL_SLICED && kind != PWQT_RESIDUAL_FLOAT_FLOAT)
+        return fail(c, PWQT_ERR_INVALID_ARG, "residual kind must be PWQT_RESIDUAL_SLICED or PWQT_RESIDUAL_FLOAT_FLOAT");
+    c->residual_kind = kind;
     return PWQT_OK;
 }
 

@@ -98,6 +98,7 @@ struct System {
     DBuf HV0, HV1;        // N and N-1 blocks: H_ii + V_ii, H_{i,i+1} + V_{i,i+1} (complex128)
     DBuf HV0f, HV1f;      // complex64 copies (mixed path)
     DBuf HV0ff, HV1ff;    // float-float splits (refinement residual)
+    DBuf ozH, ozH_rexp;   // slice tiles of the per-node [HV1^H | HV0 | HV1] panels (tensor-core residual)
     // density matrix of Sec. 3.3: N diagonal blocks and N-1 blocks (a, a+1), n x n complex128
     DBuf rho_d, rho_u;
     long long rho_energies = 0;   // energies accumulated since the last reset
@@ -129,6 +130,9 @@ namespace pwqt {
 struct Lane {
     cudaStream_t st = nullptr;
     DBuf ws_mixed, ws_jobs, ws_obs, ws_res, ws_norms;
+    // tensor-core residual: self-energy panels of the batch, their pointer table, the
+    // solution slices, column exponents and the active-energy list
+    DBuf oz_sig, oz_sig_rexp, oz_sig_tab, oz_B, oz_fexp, oz_act;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     double prof_ms = 0, prof_flops = 0, prof_phase_ms[2] = {0, 0};
     long long prof_launches = 0, prof_ir_iters = 0;
@@ -160,6 +164,8 @@ struct pwqt_ctx {
     pwqt::DBuf H0, H1, M0, M1, W;          // n x n row-major complex128; W: 6 blocks
     pwqt::DBuf M0f, M1f, H0f, H1f;         // complex64 copies
     pwqt::DBuf M0ff, M1ff;                 // float-float splits
+    pwqt::DBuf ozM, ozM_rexp;              // slice tiles of the [M1^H | M0 | M1] panel (tensor-core residual)
+    int residual_kind = PWQT_RESIDUAL_SLICED;   // refinement residual of the mixed path
     std::map<int, pwqt::System> systems;
     std::map<double, std::unique_ptr<pwqt::LeadEntry>> cache;
     // scratch reused across calls

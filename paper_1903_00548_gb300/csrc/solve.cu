@@ -186,7 +186,9 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
         ms[e] = ok ? ls[e]->m_in_s : 0;
         md[e] = ok ? ld[e]->m_in_d : 0;
     }
-    // 2. batches bounded by the device budget
+    // 2. batches bounded by the device budget (after the mixed path's per-system slice
+    // panels, which stay with the system)
+    if (precision != PWQT_FP64) PWQT_TRY(mixed_prepare(c, s, st));
     size_t free_b = 0, total_b = 0;
     PWQT_CUDA(c, cudaMemGetInfo(&free_b, &total_b));
     size_t budget = c->opts.hbm_budget_bytes ? c->opts.hbm_budget_bytes : (size_t)(0.85 * (double)free_b);

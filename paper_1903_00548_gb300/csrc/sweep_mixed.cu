@@ -12,11 +12,13 @@
 //   U-solve  32-row blocks from the bottom: diagonal block (FP32) + update above
 //            (tensor cores)  ->  XY_i = [X_i | y_i]
 // then c_i = y_i - X_i c_{i+1} (tensor cores), FP64 copy, and refinement:
-//   r = B - A c (FP64), A d = r with the stored complex64 factors, c += d.
+//   r = B - A c (FP64-accurate: exact slice products on the bf16 tensor cores,
+//   residual_oz.cu), A d = r with the stored complex64 factors, c += d.
 #include <algorithm>
 #include <cmath>
 
 #include "cgemm_tc.cuh"
+#include "residual_oz.cuh"
 #include "sweep_mixed.cuh"
 
 namespace pwqt {
@@ -521,7 +523,42 @@ __global__ void k_or_status(const SweepJob* __restrict__ jobs, const int* __rest
 size_t mixed_bytes_per_energy(int n, int N, int m) {
     // F + XY (complex64) + pivots + L scratch + FP64 solution and residual
     return sizeof(float2) * ((size_t)N * n * n + (size_t)N * n * (n + m) + (size_t)n * std::max(n, m)) + sizeof(int) * (size_t)N * n +
-           3 * sizeof(double2) * (size_t)N * n * m;   // FP64 solution, residual, float-float copy
+           3 * sizeof(double2) * (size_t)N * n * m +     // FP64 solution, residual, float-float copy
+           2 * oz::panel_item_bytes(n, 1) +               // self-energy slice panels
+           oz::b_bytes(n, N, m + 32);                     // solution slices (a column tile of slack)
+}
+
+int mixed_prepare(pwqt_ctx* c, System& s, cudaStream_t st) {
+    if (c->residual_kind != PWQT_RESIDUAL_SLICED) return PWQT_OK;
+    const int n = c->n, N = s.N;
+    const size_t nn = (size_t)n * n;
+    if (!c->ozM.p) {
+        oz::PanelSrc P{};
+        P.n = n; P.nseg = 3;
+        const double2* M0 = c->M0.as<double2>();
+        const double2* M1 = c->M1.as<double2>();
+        P.blk[0] = M1; P.ct[0] = 1; P.count[0] = 1;    // M1^H (with c_{i-1})
+        P.blk[1] = M0; P.count[1] = 1;                 // M0 (c_i)
+        P.blk[2] = M1; P.count[2] = 1;                 // M1 (c_{i+1})
+        PWQT_TRY(alloc(c, c->ozM, oz::panel_bytes(n, 1, 3)));
+        PWQT_TRY(alloc(c, c->ozM_rexp, oz::rexp_bytes(n, 1)));
+        oz::build_panel(P, 1, c->ozM_rexp.as<int>(), c->ozM.as<__nv_bfloat16>(), st);
+        c->launches += 2;
+    }
+    if (!s.ozH.p) {
+        oz::PanelSrc P{};
+        P.n = n; P.nseg = 3;
+        // item i: [HV1_{i-1}^H | HV0_i | HV1_i]; absent blocks at the ends
+        P.blk[0] = s.HV1.as<double2>(); P.stride[0] = (long long)nn; P.off[0] = -1; P.count[0] = N - 1; P.ct[0] = 1;
+        P.blk[1] = s.HV0.as<double2>(); P.stride[1] = (long long)nn; P.count[1] = N;
+        P.blk[2] = s.HV1.as<double2>(); P.stride[2] = (long long)nn; P.count[2] = N - 1;
+        PWQT_TRY(alloc(c, s.ozH, oz::panel_bytes(n, N, 3)));
+        PWQT_TRY(alloc(c, s.ozH_rexp, oz::rexp_bytes(n, N)));
+        oz::build_panel(P, N, s.ozH_rexp.as<int>(), s.ozH.as<__nv_bfloat16>(), st);
+        c->launches += 2;
+    }
+    PWQT_CUDA(c, cudaGetLastError());
+    return PWQT_OK;
 }
 
 int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJob>& jobs, SweepJob* jobs_d, std::vector<ResJob>& res,
@@ -651,11 +688,76 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
     std::vector<int> iters(nb, 0), active(nb, 1), stall(nb, 0), bits(nb, 0);
     const double tol = c->opts.ir_tol;
     PWQT_CUDA(c, cudaMemcpyAsync(active_d, active.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+
+    // ---------------- the FP64-accurate residual on the tensor cores: self-energy panels
+    // of this batch (slice tiles of Sigma_s, Sigma_d per energy), then per evaluation the
+    // solution slices of the energies still refining and four slice-product launches
+    const bool sliced = c->residual_kind == PWQT_RESIDUAL_SLICED;
+    oz::GemmArgs OG{};
+    if (sliced) {
+        if (oz::gemm_init() != 0) return fail(c, PWQT_ERR_CUDA, "slice-product GEMM set-up failed");
+        if (!c->ozM.p || !s.ozH.p) return fail(c, PWQT_ERR_STATE, "slice panels missing (mixed_prepare)");
+        std::vector<const double2*> tab(2 * nb);
+        for (int b = 0; b < nb; ++b) { tab[2 * b] = jobs[b].sig_s; tab[2 * b + 1] = jobs[b].sig_d; }
+        PWQT_TRY(ensure(c, L.oz_sig_tab, sizeof(void*) * 2 * nb));
+        PWQT_TRY(ensure(c, L.oz_sig, oz::panel_bytes(n, 2 * nb, 1)));
+        PWQT_TRY(ensure(c, L.oz_sig_rexp, oz::rexp_bytes(n, 2 * nb)));
+        PWQT_TRY(ensure(c, L.oz_B, oz::b_bytes(n, N, nb * m)));
+        PWQT_TRY(ensure(c, L.oz_fexp, sizeof(int) * (size_t)oz::col_tiles(nb * m) * 32));
+        PWQT_TRY(ensure(c, L.oz_act, sizeof(int) * nb));
+        PWQT_CUDA(c, cudaMemcpyAsync(L.oz_sig_tab.p, tab.data(), sizeof(void*) * 2 * nb, cudaMemcpyHostToDevice, st));
+        oz::PanelSrc P{};
+        P.n = n; P.nseg = 1;
+        P.tab[0] = L.oz_sig_tab.as<const double2*>();
+        oz::build_panel(P, 2 * nb, L.oz_sig_rexp.as<int>(), L.oz_sig.as<__nv_bfloat16>(), st);
+        c->launches += 2;
+        OG.n = n; OG.N = N; OG.m = m; OG.n_pad = oz::padded(n);
+        OG.B = L.oz_B.as<__nv_bfloat16>();
+        OG.fexp = L.oz_fexp.as<int>();
+        OG.act = L.oz_act.as<int>();
+        OG.jobs = res_d;
+        OG.R = S.R64;
+        OG.sC = S.sC;
+    }
+    std::vector<int> act_h;
+    auto residual = [&]() -> int {
+        if (!sliced) {
+            launch_residual_ff(RF, res_d, nb, m, active_d, st);   // energies still refining
+            c->launches += 3;
+            return PWQT_OK;
+        }
+        act_h.clear();
+        for (int b = 0; b < nb; ++b)
+            if (active[b]) act_h.push_back(b);
+        const int n_act = (int)act_h.size();
+        if (!n_act) return PWQT_OK;
+        PWQT_CUDA(c, cudaMemcpyAsync(L.oz_act.p, act_h.data(), sizeof(int) * n_act, cudaMemcpyHostToDevice, st));
+        oz::slice_solution(S.C64, S.sC, OG.act, n_act, n, N, m, L.oz_fexp.as<int>(), L.oz_B.as<__nv_bfloat16>(), st);
+        OG.n_act = n_act;
+        OG.nct = oz::col_tiles(n_act * m);
+        // r = b - E (M c): the shared M panel, one item per node
+        OG.mode = oz::MODE_M; OG.A = c->ozM.as<__nv_bfloat16>(); OG.a_item_bytes = 0; OG.rexp = c->ozM_rexp.as<int>();
+        oz::gemm(OG, N, st);
+        // r += Sigma_s c_0 and Sigma_d c_{N-1}: one item per energy and contact
+        OG.mode = oz::MODE_SIGMA; OG.A = L.oz_sig.as<__nv_bfloat16>(); OG.a_item_bytes = oz::panel_item_bytes(n, 1);
+        OG.rexp = L.oz_sig_rexp.as<int>();
+        for (int side = 0; side < 2; ++side) {
+            OG.sigma_side = side;
+            oz::gemm(OG, n_act, st);
+        }
+        // r += (HV c): one panel item per node
+        OG.mode = oz::MODE_HV; OG.A = s.ozH.as<__nv_bfloat16>(); OG.a_item_bytes = oz::panel_item_bytes(n, 3);
+        OG.rexp = s.ozH_rexp.as<int>();
+        oz::gemm(OG, N, st);
+        oz::norms(S.R64, S.sC, res_d, OG.act, n_act, n, N, m, st);
+        launch_residual_finish(res_d, nb, st, active_d);
+        c->launches += 9;
+        return PWQT_OK;
+    };
     for (int it = 0;; ++it) {
         if (c->profile) PWQT_CUDA(c, cudaEventRecord(L.ev[0], st));
         PWQT_CUDA(c, cudaMemsetAsync(res[0].rn2, 0, sizeof(double) * 2 * (size_t)nb * m, st));
-        launch_residual_ff(RF, res_d, nb, m, active_d, st);   // energies still refining
-        c->launches += 3;
+        PWQT_TRY(residual());
         if (c->profile) PWQT_CUDA(c, cudaEventRecord(L.ev[1], st));
         PWQT_CUDA(c, cudaMemcpyAsync(resid.data(), res[0].resid, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
         PWQT_CUDA(c, cudaStreamSynchronize(st));
@@ -679,9 +781,8 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
             if (!refine || resid[b] <= tol) { active[b] = 0; continue; }   // PWQT_FP32: report, do not refine
             if (resid[b] > 0.5 * prev[b]) stall[b]++;
             else stall[b] = 0;
-            // a residual that stops falling within 10 ir_tol has met the accuracy floor of
-            // the float-float residual (~2^-44 of |A||c| / |B|): converged, not flagged
-            if (stall[b] >= 2 && resid[b] <= 10.0 * tol) { active[b] = 0; continue; }
+            // a residual that stops falling above ir_tol (the floor of the residual's own
+            // accuracy, or a factorisation too poor to contract) ends refinement, flagged
             if (stall[b] >= 3 || iters[b] >= c->opts.ir_max_iters) {
                 active[b] = 0;
                 bits[b] |= PWQT_ST_IR_NO_CONVERGE;   // final residual above ir_tol
@@ -720,6 +821,7 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         if (c->profile) PWQT_CUDA(c, cudaEventRecord(L.ev[3], st));
         PWQT_CUDA(c, cudaGetLastError());
     }
+    if (sliced && oz::error_flag(true, st)) return fail(c, PWQT_ERR_TIMEOUT, "slice-product residual: a bounded mbarrier wait gave up");
     PWQT_CUDA(c, cudaMemcpyAsync(iters_dev, iters.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
     PWQT_CUDA(c, cudaMemcpyAsync(bits_d, bits.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
     k_or_status<<<(nb + 127) / 128, 128, 0, st>>>(jobs_d, bits_d, nb);

@@ -41,6 +41,8 @@ void launch_residual_ff(const ResidualFF& R, const ResJob* jobs, int nb, int m_m
 void launch_residual_finish(const ResJob* jobs, int nb, cudaStream_t st, const int* active = nullptr);
 
 size_t mixed_bytes_per_energy(int n, int N, int m);
+// slice panels of the tensor-core residual for the basis and system (once; kept)
+int mixed_prepare(pwqt_ctx* c, System& s, cudaStream_t st);
 int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJob>& jobs, SweepJob* jobs_d,
                 std::vector<ResJob>& res, ResJob* res_d, std::vector<ObsJob>& obs, ObsJob* obs_d, int nb, int* iters_dev,
                 cudaStream_t st, bool refine, Lane& lane);

@@ -22,12 +22,13 @@ ERR_TIMEOUT = -7
 INTEGRAND_CURRENT, INTEGRAND_NODE_DENSITY, INTEGRAND_NODE_DENSITY_JACOBIAN = 0, 1, 2
 FP64, MIXED, FP32 = 0, 1, 2
 ST_SINGULAR_PIVOT, ST_MODE_COUNT, ST_IR_NO_CONVERGE, ST_DEGENERATE, ST_NEAR_UNIT = 1, 2, 4, 8, 16
+RESIDUAL_SLICED, RESIDUAL_FLOAT_FLOAT = 0, 1
 
 EXPORTS = ["pwqt_create", "pwqt_destroy", "pwqt_last_error", "pwqt_assemble_intrinsic", "pwqt_set_enhancement",
            "pwqt_get_blocks", "pwqt_set_extrinsic", "pwqt_solve", "pwqt_solve_dev", "pwqt_prepare_leads",
            "pwqt_cache_info", "pwqt_bands", "pwqt_kernel_launches", "pwqt_profile", "pwqt_solve_noalloc", "pwqt_cgemm_c64",
            "pwqt_density_reset", "pwqt_accumulate_density", "pwqt_get_density_matrix", "pwqt_density_grid",
-           "pwqt_profile_refinement", "pwqt_set_refinement", "pwqt_solve_multi",
+           "pwqt_profile_refinement", "pwqt_set_refinement", "pwqt_set_residual", "pwqt_solve_multi",
            "pwqt_server_create", "pwqt_server_add_basis", "pwqt_server_submit", "pwqt_server_wait",
            "pwqt_server_stats", "pwqt_server_last_error", "pwqt_server_destroy", "pwqt_integrate",
            "pwqt_transmission_caroli", "pwqt_self_consistent", "pwqt_green_diagonal"]
@@ -103,6 +104,7 @@ def load(path: str = LIB_PATH):
     lib.pwqt_density_reset.argtypes = [P, I]
     lib.pwqt_profile_refinement.argtypes = [P, dp, dp, C.POINTER(C.c_longlong)]
     lib.pwqt_set_refinement.argtypes = [P, D, I]
+    lib.pwqt_set_residual.argtypes = [P, I]
     lib.pwqt_solve_multi.argtypes = [P, I, ip, I, dp, I, dp, dp, dp, ip, dp, dp, ip, ip]
     lib.pwqt_server_create.argtypes = [C.POINTER(P), C.POINTER(ServerOpts)]
     lib.pwqt_server_add_basis.argtypes = [P, I, C.POINTER(CellC), C.POINTER(FormFactorC), D, I, ip]
@@ -393,6 +395,11 @@ class Context:
 
     def set_refinement(self, ir_tol: float = 0.0, ir_max_iters: int = 0):
         self._check(self.lib.pwqt_set_refinement(self.h, ir_tol, ir_max_iters))
+
+    def set_residual(self, kind: int):
+        """Refinement residual of the mixed path: RESIDUAL_SLICED (tensor cores, FP64
+        accuracy; default) or RESIDUAL_FLOAT_FLOAT (FP32 pipes)."""
+        self._check(self.lib.pwqt_set_residual(self.h, kind))
 
     def profile_refinement(self):
         """(residual ms, correction ms, refinement iterations) recorded while profiling."""

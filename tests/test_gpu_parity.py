@@ -44,16 +44,25 @@ def _ctx_with_basis(pw, sys_):
 
 
 def _oracle_results(sys_, energies):
+    """Oracle results, each with its own error bar (.bar, see oracle_error)."""
     cache = {}
-    return [O.solve_energy(sys_.blk, sys_.Vd, sys_.Vu, sys_.U, float(E), cache=cache) for E in energies]
+    out = []
+    for E in energies:
+        r = O.solve_energy(sys_.blk, sys_.Vd, sys_.Vu, sys_.U, float(E), cache=cache)
+        alt = O.solve_energy(sys_.blk, sys_.Vd, sys_.Vu, sys_.U, float(E), cache=cache, reciprocal=True)
+        r.bar = O.error_bar(r, alt)
+        out.append(r)
+    return out
 
 
 def oracle_error(r):
     """The oracle's own error bar at this energy: total transmission is reciprocal
-    (T_sd = T_ds exactly for a real potential), so |T - T_ds| measures its rounding.
-    Where weakly evanescent modes (|lambda| ~ 0.96, from the basis near-null space)
-    nearly coincide, the Bloch matrix B is ill-conditioned and this reaches ~1e-8."""
-    return abs(r.T - r.T_ds)
+    (T_sd = T_ds exactly for a real potential), and the reciprocal pencil gives the
+    same modes by another rounding path, so |T - T_ds| and the spread of the two
+    solves measure its rounding.  Where weakly evanescent modes (|lambda| ~ 0.96,
+    from the basis near-null space) nearly coincide, the Bloch matrix B is
+    ill-conditioned and this reaches ~1e-8 on the chain."""
+    return r.bar
 
 
 def _compare(res_gpu, res_or, tol=TOL, absolute=False):
@@ -314,7 +323,7 @@ def test_caroli_transmission_cross_check(pw, chain):
         cache = {}
         for e, E in enumerate(Es):
             ref = O.caroli_transmission(sys_.blk, sys_.Vd, sys_.Vu, sys_.U, float(E), cache=cache)
-            bar = oracle_error(O.solve_energy(sys_.blk, sys_.Vd, sys_.Vu, sys_.U, float(E), cache=cache))
+            bar = oracle_error(_oracle_results(sys_, [E])[0])
             t = max(1e-9 * max(1.0, ref), 4 * bar)
             assert abs(Tc[e] - ref) <= t, (E, Tc[e], ref)
             assert abs(Tc[e] - res.T[e]) <= t, (E, Tc[e], res.T[e])

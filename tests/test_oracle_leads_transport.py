@@ -214,3 +214,21 @@ def test_block512_golden_values_are_physical():
         assert abs(e["T"] - e["T_ds"]) < 1e-8 * ms
         nn = np.array(e["node_n"])
         assert nn.shape == (g["n_nodes"], 2) and np.all(nn > 0)
+
+
+def test_reciprocal_pencil_gives_the_same_modes_and_transport():
+    # the error-bar route of the oracle: QZ of the pencil for mu = 1/lambda must give the
+    # same eigenvalues (to rounding) and, on the pristine chain, the same integer plateau
+    s = chain_system()
+    for E in (0.3, 1.0):
+        a = O.lead_modes(s.blk, E)
+        b = O.lead_modes(s.blk, E, reciprocal=True)
+        fa = np.sort_complex(np.where(np.isfinite(a.lam), a.lam, 0))
+        fb = np.sort_complex(np.where(np.isfinite(b.lam), b.lam, 0))
+        small = np.abs(fa) < 1e6
+        assert np.allclose(fa[small], fb[small], rtol=1e-8, atol=1e-10)
+        assert a.traveling.sum() == b.traveling.sum()
+    sp = with_potential(s, np.zeros(20))
+    for E in (0.3, 0.9):
+        r = O.solve_energy(sp.blk, sp.Vd, sp.Vu, sp.U, E, reciprocal=True)
+        assert abs(r.T - 1.0) < 1e-9 and abs(r.R) < 1e-9

@@ -101,8 +101,8 @@ def test_time_reversed_convention_gives_same_transmission(monkeypatch):
     ref = [O.solve_energy(s.blk, s.Vd, s.Vu, s.U, E).T for E in (0.4, 1.0)]
     orig = O.lead_modes
 
-    def flipped(blk, Ec):
-        m = orig(blk, Ec)
+    def flipped(blk, Ec, reciprocal=False):
+        m = orig(blk, Ec, reciprocal)
         m.dEdk = -m.dEdk
         return m
     monkeypatch.setattr(O, "lead_modes", flipped)
@@ -114,8 +114,8 @@ def test_wrong_mode_normalisation_is_caught(monkeypatch):
     # unit 2-norm instead of c^H M(lambda) c = L/2pi (Eq. normalization)
     orig = O.lead_modes
 
-    def bad(blk, Ec):
-        m = orig(blk, Ec)
+    def bad(blk, Ec, reciprocal=False):
+        m = orig(blk, Ec, reciprocal)
         for j in np.flatnonzero(m.traveling):
             m.C[:, j] /= np.linalg.norm(m.C[:, j])
         return m
@@ -137,8 +137,8 @@ def test_flipped_traveling_velocity_breaks_the_mode_count(monkeypatch):
     O.solve_energy(s.blk, s.Vd, s.Vu, s.U, 0.4)          # unmutated: count is n
     orig = O.lead_modes
 
-    def flipped_one(blk, Ec):
-        m = orig(blk, Ec)
+    def flipped_one(blk, Ec, reciprocal=False):
+        m = orig(blk, Ec, reciprocal)
         j = int(np.flatnonzero(m.traveling)[0])
         m.dEdk = m.dEdk.copy()
         m.dEdk[j] = -m.dEdk[j]

@@ -52,7 +52,7 @@ def test_noalloc_matches_allocating_solve_twice(setup):
 
 def test_noalloc_matches_oracle(setup):
     # the same energies through the oracle: 1e-9 relative (times the open channels),
-    # or four times the oracle's own reciprocity defect where that is larger
+    # or four times the oracle's own error bar where that is larger
     from oracle import pwqt_oracle as O
     torch, pwqt, wl, ctx = setup
     E = wl.energies[40:48]
@@ -62,7 +62,8 @@ def test_noalloc_matches_oracle(setup):
     cache = {}
     for e, En in enumerate(E):
         r = O.solve_energy(s.blk, s.Vd, s.Vu, s.U, float(En), cache=cache)
-        t = max(TOL * max(1.0, r.n_open_s), 4.0 * abs(r.T - r.T_ds))
+        alt = O.solve_energy(s.blk, s.Vd, s.Vu, s.U, float(En), cache=cache, reciprocal=True)
+        t = max(TOL * max(1.0, r.n_open_s), 4.0 * O.error_bar(r, alt))
         assert abs(got["T"][e] - r.T) <= t and abs(got["R"][e] - r.R) <= t, (En, got["T"][e], r.T)
 
 
