@@ -5,12 +5,19 @@ Workload (default, "ribbon512"): a 13 nm armchair ribbon (214 atoms per cell) wi
 seeded smooth potential <= 0.3 eV and the 1024-point energy grid
 [E_64 - 0.1, E_64 + 1.0] eV (~45 open channels per contact); one step solves one
 batch of energies of that grid (contact self-energies resident in the cache, built
-before timing and reported separately as sigma_cold_s_per_energy).  Default path:
-complex64 block sweep on the tensor cores + refinement; --precision fp64 times the
-complex128 path.
+before timing and reported separately as sigma_cold_s_per_energy).
+
+Default run (mixed precision, the headline `value`): complex64 block sweep on the
+tensor cores + refinement with the FP64-accurate slice-product residual, K timed
+steps of 32 energies without profiling; then one profiled step (phase and kernel
+times for the rooflines); then the FP64 GPU arm on the same box (one step of one
+energy per SM, the mixed step's energies among them; `fp64_arm`, with the largest
+|T_mixed - T_FP64| over the shared energies); then one step end to end through the
+host-buffer C ABI (`e2e`).  Meanwhile the oracle runs full 200-node solves on the
+host cores (`cpu_baseline`).  --precision fp64 times the complex128 path alone.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                [--precision mixed|fp64|auto] [--batch B] [--clocks-csv PATH]
+                [--precision mixed|fp64|auto] [--batch B] [--fp64-batch B] [--clocks-csv PATH]
 Under torchrun every rank solves its own batch (weak scaling, no data-path
 collective); the timed region is bracketed by a barrier and synchronize and the
 max over ranks is reported.
@@ -37,16 +44,6 @@ UNIT = "energy-solves/s"
 L2_BYTES = 129 * 2 ** 20
 # nominal dense rates of GB300 used to scale the measured bf16 peak to other dtypes
 NOMINAL_TFLOPS = {"bf16": 2250.0, "tf32": 1100.0, "f64": 1.25}
-# FP32 instructions per complex multiply-add of the float-float residual: four
-# float-float multiply-adds of 12 instructions each (product, its FMA error, two
-# cross terms, five for the two-sum of the leading parts, two for the low part)
-FF_INST_PER_CMAC = 48
-# DRAM bytes (read + write) of one k_residual_ff launch per (node, energy) at block 512 and
-# ~91 injected modes, from the ncu capture summarised in
-# profiles/k_residual_ff_ribbon512_n20_b8.md (1.807 GB for 20 nodes x 8 energies); the
-# kernel re-reads its blocks once per node, energy and column tile, so a full launch
-# scales with nodes x energies.  None once the kernel changes.
-RESID_DRAM_BYTES_PER_NODE_ENERGY = 1.807e9 / 160
 
 
 def peaks():
@@ -101,68 +98,84 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ----------------------------------------------------------------------------- oracle sample
-ORACLE_SAMPLE_NODES = 8
+# ----------------------------------------------------------------------------- oracle (CPU) legs
+BLAS_THREAD_VARS = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+# host memory one full-length oracle solve at block 512 holds (banded global matrix,
+# its LU and the right-hand sides), with margin
+ORACLE_BYTES_PER_WORKER = 14e9
+ORACLE_SAMPLE_NODES = 20
 
 
-def _oracle_sample(conn, wl_name, n_nodes_full, reps):
-    """Times the oracle (as it stands) on one energy of the workload with the
-    device shortened to ORACLE_SAMPLE_NODES nodes; its banded LU costs O(N), so the
-    time of a full-length solve is t * N_full / N_sample.  One BLAS thread."""
+def _mem_available():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return float(line.split()[1]) * 1024.0
+    except OSError:
+        pass
+    return 16e9
+
+
+def oracle_workers(reserve=16e9):
+    """Processes the oracle legs may run at once: one per host core, bounded by the
+    memory of full-length solves (leaving `reserve` bytes for the GPU process)."""
+    cores = os.cpu_count() or 1
+    return max(1, min(cores, int((_mem_available() - reserve) // ORACLE_BYTES_PER_WORKER)))
+
+
+def _oracle_energy(task):
+    """One oracle energy-solve, timed: the system is assembled and the contact
+    self-energies are computed first (untimed, as the GPU leg keeps them resident),
+    then the global system is solved `reps` times on a device of `nodes` nodes."""
+    wl_name, nodes, E, reps = task
     try:
         from oracle import pwqt_oracle as O
         from paper_1903_00548_gb300 import workloads as W
         wl = getattr(W, wl_name)()
-        U = W.random_smooth(ORACLE_SAMPLE_NODES)
+        U = W.random_smooth(nodes) if nodes != wl.n_nodes else wl.U
         s = O.build_system(wl.cell, wl.ff, wl.gcut, wl.n_bands, U)
-        E = float(wl.energies[len(wl.energies) // 2])
+        t0 = time.perf_counter()
         contacts = O.contacts_at(s.blk, E, U[0], U[-1])
+        t_sigma = time.perf_counter() - t0
         times = []
         for _ in range(reps):
             t0 = time.perf_counter()
             O.solve_energy(s.blk, s.Vd, s.Vu, s.U, E, contacts=contacts)
             times.append(time.perf_counter() - t0)
-        t_full = min(times) * n_nodes_full / ORACLE_SAMPLE_NODES
-        conn.send({"ok": True, "t_sample": min(times), "times": times, "t_full": t_full,
-                   "m": int(contacts[0].c_in.shape[1] + contacts[1].c_in.shape[1])})
+        return {"ok": True, "E": E, "times": times, "t_sigma": t_sigma}
     except Exception as e:  # pragma: no cover - reported in the JSON line
-        conn.send({"ok": False, "error": repr(e)})
-    conn.close()
+        return {"ok": False, "error": repr(e)}
 
 
-BLAS_THREAD_VARS = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
-
-
-def start_oracle_sample(wl_name, n_nodes_full, reps=3):
-    # the spawned child imports numpy (and starts its BLAS threads) while it re-imports
-    # this module, before _oracle_sample runs: the one-thread setting must already be in
-    # the environment it inherits
+def start_oracle_pool(wl_name, energies, nodes, reps=1, workers=None):
+    """Spawned pool (one BLAS thread per process, set in the environment the children
+    inherit before numpy starts its threads), one energy per process."""
+    workers = workers or oracle_workers()
     ctx = mp.get_context("spawn")
-    a, b = ctx.Pipe(duplex=False)
     saved = {k: os.environ.get(k) for k in BLAS_THREAD_VARS}
     for k in BLAS_THREAD_VARS:
         os.environ[k] = "1"
     try:
-        p = ctx.Process(target=_oracle_sample, args=(b, wl_name, n_nodes_full, reps), daemon=True)
-        p.start()
+        pool = ctx.Pool(workers)
+        tasks = [(wl_name, nodes, float(E), reps) for E in energies[:workers]]
+        res = pool.map_async(_oracle_energy, tasks)
     finally:
         for k, v in saved.items():
             if v is None:
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
-    return p, a
+    return pool, res, workers
 
 
-def finish_oracle_sample(p, conn, timeout=900):
-    if conn.poll(timeout):
-        r = conn.recv()
-    else:
-        r = {"ok": False, "error": "oracle sample timed out"}
-    p.join(timeout=5)
-    if p.is_alive():
-        p.kill()
-    return r
+def finish_oracle_pool(pool, res, timeout=1500):
+    try:
+        out = res.get(timeout)
+    except Exception as e:
+        out = [{"ok": False, "error": f"oracle pool: {e!r}"}]
+    pool.terminate()
+    pool.join()
+    return out
 
 
 # ----------------------------------------------------------------------------- distributed
@@ -207,133 +220,176 @@ def shard_energies(grid, batch, rank, world):
 
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args, world, rank):
+    """The oracle as it stands, on the host cores: one energy per process, each step
+    a banded solve of a shortened device (ORACLE_SAMPLE_NODES nodes; the solve's cost
+    is linear in the node count, which the default run's cpu_baseline checks against
+    full-length solves), so that the whole run ends within minutes."""
     if rank != 0:
         return 0
     from paper_1903_00548_gb300 import workloads as W
     wl = getattr(W, args.workload)()
-    p, conn = start_oracle_sample(args.workload, wl.n_nodes, reps=args.warmup + args.steps)
-    r = finish_oracle_sample(p, conn)
-    if not r.get("ok"):
-        print(json.dumps({"impl": "reference", "unavailable": r.get("error", "oracle failed")}))
+    E = shard_energies(wl.energies, 32, 0, 1)
+    pool, res, workers = start_oracle_pool(args.workload, E, ORACLE_SAMPLE_NODES, reps=args.warmup + args.steps)
+    out = finish_oracle_pool(pool, res)
+    ok = [r for r in out if r.get("ok")]
+    if not ok:
+        print(json.dumps({"impl": "reference", "unavailable": out[0].get("error", "oracle failed")}))
         return 0
-    ts = r["times"][args.warmup:] or r["times"]
-    t_full = statistics.mean(ts) * wl.n_nodes / ORACLE_SAMPLE_NODES
-    value = 1.0 / t_full
-    sample = (f"one energy of {args.workload} (n={wl.n}) on {ORACLE_SAMPLE_NODES} of {wl.n_nodes} nodes per step, "
-              f"banded-LU time scaled by {wl.n_nodes}/{ORACLE_SAMPLE_NODES}; contact self-energies built before timing")
+    # step k: every process solves its energy once; the step lasts as long as the slowest
+    steps = [max(r["times"][k] for r in ok) for k in range(args.warmup, args.warmup + args.steps)]
+    t_step = statistics.mean(steps) * wl.n_nodes / ORACLE_SAMPLE_NODES
+    value = len(ok) / t_step
+    sample = (f"{len(ok)} processes (one BLAS thread each), one energy of {args.workload} (n={wl.n}) per process and "
+              f"step, banded solve of {ORACLE_SAMPLE_NODES} of {wl.n_nodes} nodes scaled by {wl.n_nodes}/"
+              f"{ORACLE_SAMPLE_NODES}; contact self-energies computed before timing")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_full,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "n": wl.n, "nodes": wl.n_nodes},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value, "unit": UNIT},
+            "cpu_baseline": {"kind": "oracle", "cores": len(ok), "sample": sample, "value": value, "unit": UNIT},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
 # ----------------------------------------------------------------------------- our arm
+def fp64_energies(grid, E_mixed, total):
+    """`total` energies for the FP64 arm (one per SM): the mixed step's own energies
+    and the rest spread over the grid between them."""
+    extra = [e for e in shard_energies(grid, total, 0, 1) if e not in set(E_mixed.tolist())]
+    keep = max(0, total - len(E_mixed))
+    idx = np.linspace(0, len(extra) - 1, keep).round().astype(int) if keep and extra else np.array([], int)
+    return np.sort(np.concatenate([E_mixed, np.asarray(extra)[idx]]))
+
+
+def timed_steps(step, stream, steps):
+    """CUDA-event time of `steps` calls on `stream` (synchronised on both sides)."""
+    import torch
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    marks = []
+    a.record(stream)
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        marks.append((e0, e1))
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b), [x.elapsed_time(y) for x, y in marks]
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_1903_00548_gb300 import build as B
     from paper_1903_00548_gb300 import pwqt as pw
     from paper_1903_00548_gb300 import workloads as W
 
-    B.build()
     wl = getattr(W, args.workload)()
     if args.nodes:
         wl.n_nodes = args.nodes
         wl.U = W.random_smooth(args.nodes)
-    prec_name = args.precision
-    if prec_name == "auto":
-        prec_name = "mixed"
+    prec_name = "mixed" if args.precision == "auto" else args.precision
     prec = pw.MIXED if prec_name == "mixed" else pw.FP64
-    batch = args.batch or (152 if prec == pw.FP64 else 32)
+    batch = args.batch or (32 if prec == pw.MIXED else 152)
     n_grid = len(wl.energies)
     E = shard_energies(wl.energies, batch, rank, world)
 
-    oracle_proc = None
+    # the oracle on the host cores: full-length solves, one energy per process, started
+    # first (spawned; it runs while the GPU legs do)
+    oracle = None
     if rank == 0 and not args.no_cpu_baseline:
-        oracle_proc = start_oracle_sample(args.workload, wl.n_nodes)
+        oracle = start_oracle_pool(args.workload, E, wl.n_nodes, reps=1)
 
+    B.build()
     torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp64_batch = args.fp64_batch if args.fp64_batch >= 0 else sms
+    E64 = fp64_energies(wl.energies, E, fp64_batch) if (prec == pw.MIXED and fp64_batch > 0) else np.zeros(0)
+
     ctx = pw.Context(device=local)
     t0 = time.perf_counter()
     n = ctx.assemble_intrinsic(wl.cell, wl.ff, wl.gcut, wl.n_bands)
     ctx.set_extrinsic(0, wl.U)
     t_setup = time.perf_counter() - t0
+    E_all = np.union1d(E, E64)
     t0 = time.perf_counter()
-    ctx.prepare_leads(0, E)
+    ctx.prepare_leads(0, E_all)
     t_leads = time.perf_counter() - t0
 
-    dev = torch.device("cuda", local)
     N = wl.n_nodes
-    outs = {
-        "T": torch.empty(batch, dtype=torch.float64, device=dev),
-        "R": torch.empty(batch, dtype=torch.float64, device=dev),
-        "T_ds": torch.empty(batch, dtype=torch.float64, device=dev),
-        "n_open": torch.empty(2 * batch, dtype=torch.int32, device=dev),
-        "node_n": torch.empty(batch * N * 2, dtype=torch.float64, device=dev),
-        "resid": torch.empty(batch, dtype=torch.float64, device=dev),
-        "iters": torch.empty(batch, dtype=torch.int32, device=dev),
-        "status": torch.empty(batch, dtype=torch.int32, device=dev),
-    }
+    def outs_for(nb):
+        return {"T": torch.empty(nb, dtype=torch.float64, device=dev), "R": torch.empty(nb, dtype=torch.float64, device=dev),
+                "T_ds": torch.empty(nb, dtype=torch.float64, device=dev),
+                "n_open": torch.empty(2 * nb, dtype=torch.int32, device=dev),
+                "node_n": torch.empty(nb * N * 2, dtype=torch.float64, device=dev),
+                "resid": torch.empty(nb, dtype=torch.float64, device=dev),
+                "iters": torch.empty(nb, dtype=torch.int32, device=dev),
+                "status": torch.empty(nb, dtype=torch.int32, device=dev)}
+    outs = outs_for(batch)
     ptrs = {k: v.data_ptr() for k, v in outs.items()}
     stream = torch.cuda.Stream(device=dev)
 
     def step():
         ctx.solve_dev(0, E, prec, ptrs, stream.cuda_stream)
 
+    # ---- headline: unprofiled timed steps
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
-    ctx.profile(True, reset=True)
     launches0 = ctx.kernel_launches()
     clocks = Clocks(local, args.clocks_csv.format(rank=rank))
     barrier(world)
-    torch.cuda.synchronize(dev)
-    ev_s = torch.cuda.Event(enable_timing=True)
-    ev_e = torch.cuda.Event(enable_timing=True)
-    step_ms = []
-    ev_s.record(stream)
-    for _ in range(args.steps):
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        step()
-        b.record(stream)
-        step_ms.append((a, b))
-    ev_e.record(stream)
-    torch.cuda.synchronize(dev)
+    total_ms, per_step = timed_steps(step, stream, args.steps)
     barrier(world)
     clk_info = clocks.stop()
-    total_ms = ev_s.elapsed_time(ev_e)
-    per_step = [a.elapsed_time(b) for a, b in step_ms]
     launches = (ctx.kernel_launches() - launches0) // max(1, args.steps)
-    ir_res_ms, ir_cor_ms, ir_iters = ctx.profile_refinement()
-    sweep_ms, sweep_n, sweep_flops = ctx.profile(False)
     total_ms = max_over_ranks(world, total_ms)
     value = world * batch * args.steps / (total_ms / 1e3)
-
-    # results of the last step: statuses, refinement, residuals
     status = outs["status"].cpu().numpy()
     iters = outs["iters"].cpu().numpy()
     resid = outs["resid"].cpu().numpy()
     nopen = outs["n_open"].cpu().numpy().reshape(batch, 2)
+    T_step = outs["T"].cpu().numpy()
 
-    # end to end through the host-buffer C ABI (copies inside the timed region)
-    e2e_steps = 1
+    # ---- one more step with CUDA-event profiling (phases and kernel times for the roofline)
+    ctx.profile(True, reset=True)
+    prof_ms, _ = timed_steps(step, stream, 1)
+    ir_res_ms, ir_cor_ms, ir_iters = ctx.profile_refinement()
+    oz_ms, oz_cmacs, oz_mma, oz_launches = ctx.profile_residual()
+    sweep_ms, sweep_n, sweep_flops = ctx.profile(False)
+
+    # ---- the FP64 GPU arm on the same box: one energy per SM, the mixed step's energies among them
+    fp64 = None
+    if len(E64):
+        o64 = outs_for(len(E64))
+        p64 = {k: v.data_ptr() for k, v in o64.items()}
+        ctx.solve_dev(0, E64[:1], pw.FP64, p64, stream.cuda_stream)          # warm-up (one energy)
+        clocks64 = Clocks(local, args.clocks_csv.format(rank=f"{rank}_fp64"))
+        ms64, _ = timed_steps(lambda: ctx.solve_dev(0, E64, pw.FP64, p64, stream.cuda_stream), stream, 1)
+        clk64 = clocks64.stop()
+        T64 = o64["T"].cpu().numpy()
+        st64 = o64["status"].cpu().numpy()
+        pos = np.searchsorted(E64, E)
+        dT = np.abs(T_step - T64[pos])
+        fp64 = {"value": world * len(E64) / (ms64 / 1e3), "unit": UNIT, "energies": int(len(E64)),
+                "ms": ms64, "clocks": clk64, "status_nonzero": int(np.count_nonzero(st64 & 7)),
+                "max_abs_dT_mixed_vs_fp64": float(np.max(dT)), "mean_abs_dT_mixed_vs_fp64": float(np.mean(dT))}
+
+    # ---- end to end through the host-buffer C ABI (copies inside the timed region)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        res = ctx.solve(0, E, prec)
-    t_e2e = time.perf_counter() - t0
-    t_e2e = max_over_ranks(world, t_e2e)
-    e2e_value = world * batch * e2e_steps / t_e2e
+    res = ctx.solve(0, E, prec)
+    t_e2e = max_over_ranks(world, time.perf_counter() - t0)
+    e2e_value = world * batch / t_e2e
     h2d = 8 * batch
     d2h = batch * (8 * 4 + 4 * 4 + 8 * 2 * N)
 
-    # density-matrix route (reported apart from the energy-solve metric): one more
-    # solve of the same energies with the rank-m accumulation, then n(r) on a grid
+    # ---- density-matrix route (reported apart from the energy-solve metric)
     dens = None
     if not args.no_density:
         w = np.full(len(E), (wl.energies[1] - wl.energies[0]) if len(wl.energies) > 1 else 1.0)
@@ -351,59 +407,59 @@ def run_ours(args, world, rank, local):
                 "solve_plus_accumulate_s": t_acc, "grid_s": t_grid, "grid": [nx, nz],
                 "grid_points": int(grid.size), "n_max": float(grid.max())}
 
-    # roofline of the block sweep (tensor cores on the mixed path, FP64 pipe otherwise)
+    # ---- rooflines (algorithmic work; peaks from MEASURED_PEAKS.json)
     bf16, hbm, src = peaks()
-    dtype = "f64" if prec == pw.FP64 else "tf32"
-    peak = bf16 * NOMINAL_TFLOPS[dtype] / NOMINAL_TFLOPS["bf16"]
-    achieved = (sweep_flops / max(sweep_n, 1)) / (sweep_ms / max(sweep_n, 1) / 1e3) / 1e12 if sweep_n else None
-    roof_sweep = {"bound": "tensor" if prec == pw.MIXED else "fp64", "achieved": achieved, "peak": peak,
-                  "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
-                  "kernel": "k_sweep_fp64" if prec == pw.FP64 else "block sweep (k_cgemm_tc + k_mx_panel + k_mx_trsm_up)",
-                  "peak_source": f"{src} bf16 x nominal {dtype}/bf16 ratio",
-                  "flops_per_launch": sweep_flops / max(sweep_n, 1), "avg_launch_ms": sweep_ms / max(sweep_n, 1),
-                  "launches": sweep_n}
-    roof = roof_sweep
-    if prec == pw.MIXED and ir_res_ms > 0:
-        # the dominant kernel of the mixed path: the float-float residual on the FP32 pipes.
-        # Algorithmic work per evaluation and energy: (3N - 2) n^2 m complex MACs (the
-        # block-tridiagonal rows), FF_INST_PER_CMAC FP32 instructions each; evaluations per
-        # energy = refinement iterations + 1.  Peak: one FP32 instruction per lane per clock.
-        m_e = nopen.sum(1).astype(np.float64)
-        evals = iters.astype(np.float64) + 1.0
-        inst = float(np.sum(evals * m_e)) * (3 * N - 2) * float(n) * n * FF_INST_PER_CMAC
-        launches_res = float(np.max(evals))
-        sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        clk = (clk_info.get("sm_max_mhz") or 2070.0) * 1e6
-        peak_alu = sms * 128 * clk / 1e12
-        res_ms_step = ir_res_ms / args.steps
-        ach = inst / (res_ms_step / 1e3) / 1e12
-        traffic = None
-        if RESID_DRAM_BYTES_PER_NODE_ENERGY is not None and n == 512:
-            traffic = RESID_DRAM_BYTES_PER_NODE_ENERGY * N * float(np.sum(evals)) / launches_res
-        roof = {"bound": "alu", "achieved": ach, "peak": peak_alu, "unit": "T FP32 instructions/s",
-                "frac": ach / peak_alu, "traffic": traffic, "traffic_unit": "bytes per launch (ncu, scaled)",
-                "kernel": "k_residual_ff",
-                "peak_source": f"{sms} SMs x 128 FP32 lanes x {clk / 1e6:.0f} MHz (max SM clock)",
-                "inst_per_launch": inst / launches_res, "avg_launch_ms": res_ms_step / launches_res,
-                "launches": launches_res * args.steps, "inst_per_complex_mac": FF_INST_PER_CMAC}
+    tf32 = bf16 * NOMINAL_TFLOPS["tf32"] / NOMINAL_TFLOPS["bf16"]
+    f64_peak = bf16 * NOMINAL_TFLOPS["f64"] / NOMINAL_TFLOPS["bf16"]
+    sweep_alg = (56.0 / 3.0) * N * float(n) ** 3 * batch
+    roof_sweep = {"bound": "tensor" if prec == pw.MIXED else "fp64",
+                  "achieved": sweep_alg / (sweep_ms / 1e3) / 1e12 if sweep_ms else None,
+                  "peak": tf32 if prec == pw.MIXED else f64_peak, "unit": "TFLOP/s",
+                  "kernel": "block sweep (k_cgemm_tc + k_mx_panel + k_mx_trsm_up)" if prec == pw.MIXED else "k_sweep_fp64",
+                  "work": "(56/3) N n^3 real flop per energy (complex LU, X_i solve, Schur product)",
+                  "peak_source": f"{src} bf16 x nominal {'tf32' if prec == pw.MIXED else 'f64'}/bf16", "traffic": None,
+                  "ms_per_step": sweep_ms, "launches": sweep_n}
+    if roof_sweep["achieved"]:
+        roof_sweep["frac"] = roof_sweep["achieved"] / roof_sweep["peak"]
+    roof_res = None
+    if oz_ms > 0:
+        ach = oz_mma / (oz_ms / 1e3) / 1e12
+        roof_res = {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
+                    "kernel": "k_oz_gemm (slice-product residual)",
+                    "work": "bf16 MMA flops of the 34 exact slice products per real product (7-bit slices, "
+                            "split form E M c - HV c - Sigma c)",
+                    "peak_source": f"{src} bf16 (burst)", "traffic": None,
+                    "fp64_equivalent": {"achieved": 8 * oz_cmacs / (oz_ms / 1e3) / 1e12, "unit": "TFLOP/s",
+                                        "work": "8 real flop per complex MAC of B - A c (3 N n^2 per column)",
+                                        "fp64_pipe_peak": f64_peak},
+                    "ms_per_step": oz_ms, "launches": oz_launches}
+    phases = {"sweep": sweep_ms, "residual": ir_res_ms, "correction": ir_cor_ms}
+    dominant = max(phases, key=phases.get)
+    roof = roof_res if (roof_res and dominant == "residual") else roof_sweep
+    if dominant == "correction":
+        roof = dict(roof_res or roof_sweep)
+        roof["note"] = ("the correction solves (k_mx_lusolve, latency-bound) take the largest share of the step; "
+                        "this object describes the larger of the tensor-core phases")
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == pw.FP64 else "c64 (3xTF32 tensor cores) + float-float residual",
+            "dtype": "f64" if prec == pw.FP64 else "c64 (3xTF32 tensor cores) + FP64-accurate residual (bf16 slice products)",
             "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "nodes": N, "energies_per_step": batch,
                        "energy_grid": n_grid, "precision": prec_name, "l2": "inputs larger than L2 "
-                       f"(factor panels {N * n * n * 16 * batch / 1e9:.0f} GB per step)"},
+                       f"(factor panels {N * n * n * 8 * batch / 1e9:.0f} GB per step)"},
             "latency_ms": {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99)),
                            "unit": f"per step of {batch} energies"},
-            "sigma_cold_s_per_energy": t_leads / max(1, len(set(E.tolist()))), "setup_s": t_setup,
+            "fp64_arm": fp64,
+            "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
+            "sigma_cold_s_per_energy": t_leads / max(1, len(E_all)), "setup_s": t_setup,
             "gpu_launches": int(launches), "clocks": clk_info, "roofline": roof, "roofline_sweep": roof_sweep,
-            "density": dens,
-            "phases_ms_per_step": {"sweep": sweep_ms / args.steps, "refine_residual": ir_res_ms / args.steps,
-                                   "refine_correction": ir_cor_ms / args.steps,
-                                   "refine_iterations": ir_iters / args.steps,
-                                   "note": "CUDA events; profiling serialises the host with each phase"},
+            "roofline_residual": roof_res, "density": dens,
+            "phases_ms_per_step": {"sweep": sweep_ms, "refine_residual": ir_res_ms, "refine_correction": ir_cor_ms,
+                                   "refine_iterations": ir_iters, "profiled_step_ms": prof_ms,
+                                   "note": "one extra step with CUDA events, after the timed steps; the two halves "
+                                           "of the batch run on two streams, so phase sums can exceed the step"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "results": {"max_resid": float(np.max(resid)), "max_iters": int(np.max(iters)),
                         "status_nonzero": int(np.count_nonzero(status)),
@@ -413,16 +469,20 @@ def run_ours(args, world, rank, local):
                         "max_resid_unflagged": float(np.max(resid[(status & 7) == 0])) if np.any((status & 7) == 0) else None,
                         "mean_modes": float(nopen.sum(1).mean()),
                         "T_mean": float(np.mean(res.T))}}
-    if oracle_proc is not None:
-        r = finish_oracle_sample(*oracle_proc)
-        if r.get("ok"):
-            line["cpu_baseline"] = {"value": 1.0 / r["t_full"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": f"one energy of {args.workload} on {ORACLE_SAMPLE_NODES} of {N} "
-                                              f"nodes, banded-LU time scaled by {N}/{ORACLE_SAMPLE_NODES} "
-                                              f"(t_sample {r['t_sample']:.2f} s), self-energies built untimed"}
+    if oracle is not None:
+        out = finish_oracle_pool(oracle[0], oracle[1])
+        ok = [r for r in out if r.get("ok")]
+        if ok:
+            t_solve = statistics.mean(r["times"][0] for r in ok)
+            line["cpu_baseline"] = {
+                "value": len(ok) / t_solve, "unit": UNIT, "cores": len(ok), "kind": "oracle",
+                "sample": f"{len(ok)} processes (one BLAS thread each) on {os.cpu_count()} host cores, one full "
+                          f"{N}-node energy-solve of {args.workload} each (banded LU of the global system, "
+                          f"mean {t_solve:.1f} s); contact self-energies computed first, untimed "
+                          f"(mean {statistics.mean(r['t_sigma'] for r in ok):.1f} s per energy)"}
         else:
-            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": "failed: " + r.get("error", "?")}
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle",
+                                    "sample": "failed: " + out[0].get("error", "?")}
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
@@ -534,6 +594,8 @@ def main(argv=None):
     ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64"])
     ap.add_argument("--workload", default="ribbon512")
     ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--fp64-batch", type=int, default=-1,
+                    help="energies of the FP64 arm (default: one per SM; 0 skips it)")
     ap.add_argument("--nodes", type=int, default=0, help="development only: shorter device")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-density", action="store_true", help="skip the density-matrix timing")

@@ -248,6 +248,15 @@ int pwqt_profile_refinement(pwqt_ctx* ctx, double* residual_ms, double* correcti
  *     (~48-bit significand; floor ~4e-10 ||B|| at block 512).
  * Errors: PWQT_ERR_INVALID_ARG for any other value.
  */
+/*
+ * Slice-product residual launches recorded while pwqt_profile is enabled (same
+ * reset; the paper has no counterpart): CUDA-event milliseconds of the launches
+ * (summed over the halves of a mixed batch), the method's complex multiply-adds
+ * (3 N n^2 per solution column and evaluation), the bf16 MMA flops of the 34 kept
+ * slice products, and the launch count.  Any pointer may be NULL.
+ */
+int pwqt_profile_residual(pwqt_ctx* ctx, double* ms, double* cmacs, double* mma_flops, long long* launches);
+
 #define PWQT_RESIDUAL_SLICED       0
 #define PWQT_RESIDUAL_FLOAT_FLOAT  1
 int pwqt_set_residual(pwqt_ctx* ctx, int kind);

@@ -32,13 +32,18 @@ int Lane::init(int dev) {
         return PWQT_ERR_CUDA;
     for (auto& e : ev)
         if (cudaEventCreate(&e) != cudaSuccess) return PWQT_ERR_CUDA;
+    for (auto& e : oz_ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return PWQT_ERR_CUDA;
     return PWQT_OK;
 }
 
 void Lane::destroy() {
     if (st) cudaStreamSynchronize(st);
     ws_mixed.release(); ws_jobs.release(); ws_obs.release(); ws_res.release(); ws_norms.release();
+    oz_sig.release(); oz_sig_rexp.release(); oz_sig_tab.release(); oz_B.release(); oz_fexp.release(); oz_act.release();
     for (auto& e : ev)
+        if (e) cudaEventDestroy(e), e = nullptr;
+    for (auto& e : oz_ev)
         if (e) cudaEventDestroy(e), e = nullptr;
     if (st) cudaStreamDestroy(st);
     st = nullptr;

@@ -270,6 +270,7 @@ int pwqt_profile(pwqt_ctx* c, int enable, double* sweep_ms, long long* sweep_lau
     if (reset) {
         c->prof_ms = 0; c->prof_launches = 0; c->prof_flops = 0;
         c->prof_phase_ms[0] = c->prof_phase_ms[1] = 0; c->prof_ir_iters = 0;
+        c->prof_oz_ms = c->prof_oz_cmacs = c->prof_oz_mma_flops = 0; c->prof_oz_launches = 0;
     }
     return PWQT_OK;
 }
@@ -375,6 +376,15 @@ int pwqt_set_refinement(pwqt_ctx* c, double ir_tol, int ir_max_iters) {
         return fail(c, PWQT_ERR_INVALID_ARG, "ir_tol must be finite and >= 0, ir_max_iters >= 0");
     c->opts.ir_tol = ir_tol > 0 ? ir_tol : 1e-10;
     c->opts.ir_max_iters = ir_max_iters > 0 ? ir_max_iters : 40;
+    return PWQT_OK;
+}
+
+int pwqt_profile_residual(pwqt_ctx* c, double* ms, double* cmacs, double* mma_flops, long long* launches) {
+    PWQT_TRY(check_ctx(c));
+    if (ms) *ms = c->prof_oz_ms;
+    if (cmacs) *cmacs = c->prof_oz_cmacs;
+    if (mma_flops) *mma_flops = c->prof_oz_mma_flops;
+    if (launches) *launches = c->prof_oz_launches;
     return PWQT_OK;
 }
 

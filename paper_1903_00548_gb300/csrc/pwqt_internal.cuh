@@ -134,8 +134,13 @@ struct Lane {
     // solution slices, column exponents and the active-energy list
     DBuf oz_sig, oz_sig_rexp, oz_sig_tab, oz_B, oz_fexp, oz_act;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t oz_ev[2] = {nullptr, nullptr};   // around the slice-product launches of one residual
     double prof_ms = 0, prof_flops = 0, prof_phase_ms[2] = {0, 0};
     long long prof_launches = 0, prof_ir_iters = 0;
+    // slice-product residual: event time, the method's complex MACs (3 N n^2 per column),
+    // bf16 MMA flops issued for the 34 kept slice pairs, launches
+    double prof_oz_ms = 0, prof_oz_cmacs = 0, prof_oz_mma_flops = 0;
+    long long prof_oz_launches = 0;
     int init(int dev);      // stream and events on first use
     void destroy();
 };
@@ -182,6 +187,8 @@ struct pwqt_ctx {
     // refinement phases of the mixed path: [0] residuals, [1] corrections; iterations
     double prof_phase_ms[2] = {0.0, 0.0};
     long long prof_ir_iters = 0;
+    double prof_oz_ms = 0, prof_oz_cmacs = 0, prof_oz_mma_flops = 0;
+    long long prof_oz_launches = 0;
     cudaEvent_t ev2 = nullptr, ev3 = nullptr;
     // host threads that fill the contact cache concurrently
     int lead_threads = 8;

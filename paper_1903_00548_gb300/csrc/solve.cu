@@ -347,9 +347,12 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
             for (auto& L : c->lanes) {
                 c->prof_ms += L.prof_ms; c->prof_flops += L.prof_flops; c->prof_launches += L.prof_launches;
                 c->prof_phase_ms[0] += L.prof_phase_ms[0]; c->prof_phase_ms[1] += L.prof_phase_ms[1];
+                c->prof_oz_ms += L.prof_oz_ms; c->prof_oz_cmacs += L.prof_oz_cmacs;
+                c->prof_oz_mma_flops += L.prof_oz_mma_flops; c->prof_oz_launches += L.prof_oz_launches;
                 it_max = std::max(it_max, L.prof_ir_iters);
                 L.prof_ms = L.prof_flops = L.prof_phase_ms[0] = L.prof_phase_ms[1] = 0;
-                L.prof_launches = L.prof_ir_iters = 0;
+                L.prof_oz_ms = L.prof_oz_cmacs = L.prof_oz_mma_flops = 0;
+                L.prof_launches = L.prof_ir_iters = L.prof_oz_launches = 0;
             }
             c->prof_ir_iters += it_max;
         }

@@ -735,6 +735,7 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         oz::slice_solution(S.C64, S.sC, OG.act, n_act, n, N, m, L.oz_fexp.as<int>(), L.oz_B.as<__nv_bfloat16>(), st);
         OG.n_act = n_act;
         OG.nct = oz::col_tiles(n_act * m);
+        if (c->profile) PWQT_CUDA(c, cudaEventRecord(L.oz_ev[0], st));
         // r = b - E (M c): the shared M panel, one item per node
         OG.mode = oz::MODE_M; OG.A = c->ozM.as<__nv_bfloat16>(); OG.a_item_bytes = 0; OG.rexp = c->ozM_rexp.as<int>();
         oz::gemm(OG, N, st);
@@ -749,6 +750,21 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         OG.mode = oz::MODE_HV; OG.A = s.ozH.as<__nv_bfloat16>(); OG.a_item_bytes = oz::panel_item_bytes(n, 3);
         OG.rexp = s.ozH_rexp.as<int>();
         oz::gemm(OG, N, st);
+        if (c->profile) {
+            PWQT_CUDA(c, cudaEventRecord(L.oz_ev[1], st));
+            // work of these launches: the method's complex MACs (3N - 2 block products and
+            // the two self-energies per column) and the bf16 MMA flops of the kept pairs
+            // (34 slice products of 128 x 32 x 16 per 16 real K and 32 columns)
+            double cols = 0;
+            for (int b : act_h) cols += jobs[b].ms + jobs[b].md;
+            L.prof_oz_cmacs += (double)(3 * N) * n * (double)n * cols;
+            const double kreal_nodes = 2.0 * (3 * N - 2) * 2 * oz::padded(n);   // M and HV launches
+            double sig_tiles = 0;
+            for (int k = 0; k < n_act; ++k) sig_tiles += (k * m + m - 1) / 32 - (k * m) / 32 + 1;
+            const double rt = 2.0 * oz::padded(n) / 128;
+            L.prof_oz_mma_flops += (kreal_nodes * OG.nct + 2.0 * sig_tiles * 2 * oz::padded(n)) * rt * 34.0 * 32 * 128 * 2;
+            L.prof_oz_launches += 4;
+        }
         oz::norms(S.R64, S.sC, res_d, OG.act, n_act, n, N, m, st);
         launch_residual_finish(res_d, nb, st, active_d);
         c->launches += 9;
@@ -765,6 +781,10 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
             float ms = 0;
             cudaEventElapsedTime(&ms, L.ev[0], L.ev[1]);
             L.prof_phase_ms[0] += ms;
+            if (sliced && !act_h.empty()) {
+                cudaEventElapsedTime(&ms, L.oz_ev[0], L.oz_ev[1]);
+                L.prof_oz_ms += ms;
+            }
             if (it > 0) {
                 cudaEventElapsedTime(&ms, L.ev[2], L.ev[3]);
                 L.prof_phase_ms[1] += ms;

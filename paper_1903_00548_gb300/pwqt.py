@@ -28,7 +28,7 @@ EXPORTS = ["pwqt_create", "pwqt_destroy", "pwqt_last_error", "pwqt_assemble_intr
            "pwqt_get_blocks", "pwqt_set_extrinsic", "pwqt_solve", "pwqt_solve_dev", "pwqt_prepare_leads",
            "pwqt_cache_info", "pwqt_bands", "pwqt_kernel_launches", "pwqt_profile", "pwqt_solve_noalloc", "pwqt_cgemm_c64",
            "pwqt_density_reset", "pwqt_accumulate_density", "pwqt_get_density_matrix", "pwqt_density_grid",
-           "pwqt_profile_refinement", "pwqt_set_refinement", "pwqt_set_residual", "pwqt_solve_multi",
+           "pwqt_profile_refinement", "pwqt_set_refinement", "pwqt_set_residual", "pwqt_profile_residual", "pwqt_solve_multi",
            "pwqt_server_create", "pwqt_server_add_basis", "pwqt_server_submit", "pwqt_server_wait",
            "pwqt_server_stats", "pwqt_server_last_error", "pwqt_server_destroy", "pwqt_integrate",
            "pwqt_transmission_caroli", "pwqt_self_consistent", "pwqt_green_diagonal"]
@@ -105,6 +105,7 @@ def load(path: str = LIB_PATH):
     lib.pwqt_profile_refinement.argtypes = [P, dp, dp, C.POINTER(C.c_longlong)]
     lib.pwqt_set_refinement.argtypes = [P, D, I]
     lib.pwqt_set_residual.argtypes = [P, I]
+    lib.pwqt_profile_residual.argtypes = [P, dp, dp, dp, C.POINTER(C.c_longlong)]
     lib.pwqt_solve_multi.argtypes = [P, I, ip, I, dp, I, dp, dp, dp, ip, dp, dp, ip, ip]
     lib.pwqt_server_create.argtypes = [C.POINTER(P), C.POINTER(ServerOpts)]
     lib.pwqt_server_add_basis.argtypes = [P, I, C.POINTER(CellC), C.POINTER(FormFactorC), D, I, ip]
@@ -400,6 +401,14 @@ class Context:
         """Refinement residual of the mixed path: RESIDUAL_SLICED (tensor cores, FP64
         accuracy; default) or RESIDUAL_FLOAT_FLOAT (FP32 pipes)."""
         self._check(self.lib.pwqt_set_residual(self.h, kind))
+
+    def profile_residual(self):
+        """(ms, complex MACs, bf16 MMA flops, launches) of the slice-product residual
+        launches recorded while profiling was on."""
+        ms, cm, fl = C.c_double(), C.c_double(), C.c_double()
+        n = C.c_longlong()
+        self._check(self.lib.pwqt_profile_residual(self.h, C.byref(ms), C.byref(cm), C.byref(fl), C.byref(n)))
+        return ms.value, cm.value, fl.value, n.value
 
     def profile_refinement(self):
         """(residual ms, correction ms, refinement iterations) recorded while profiling."""

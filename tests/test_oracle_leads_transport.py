@@ -216,6 +216,28 @@ def test_block512_golden_values_are_physical():
         assert nn.shape == (g["n_nodes"], 2) and np.all(nn > 0)
 
 
+def test_full_size_golden_values_are_physical():
+    # the stored 200-node expectations (tests/golden/make_ribbon512_full.py): flux
+    # conservation, reciprocity, both pencils agreeing within the stored bar, positive
+    # node densities, and the energies are the bench step's own
+    import json
+    import os
+
+    import bench
+    g = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ribbon512_n200.json")))
+    wl = W.ribbon512()
+    assert g["n"] == 512 and g["n_nodes"] == 200 and np.allclose(g["U"], wl.U, rtol=0, atol=1e-15)
+    E = bench.shard_energies(wl.energies, 32, 0, 1)
+    for k, e in zip(g["step_entries"], g["energies"]):
+        assert abs(E[k] - e["E"]) < 1e-12
+        ms = e["n_open"][0]
+        assert ms == e["n_open"][1] and ms > 0
+        assert abs(e["T"] + e["R"] - ms) < 1e-8 * ms
+        assert abs(e["T"] - e["T_ds"]) <= e["bar"] and abs(e["T"] - e["T_reciprocal"]) <= e["bar"] < 1e-8
+        nn = np.array(e["node_n"])
+        assert nn.shape == (200, 2) and np.all(nn > 0)
+
+
 def test_reciprocal_pencil_gives_the_same_modes_and_transport():
     # the error-bar route of the oracle: QZ of the pencil for mu = 1/lambda must give the
     # same eigenvalues (to rounding) and, on the pristine chain, the same integer plateau
