@@ -170,11 +170,16 @@ int pwqt_solve(pwqt_ctx* ctx, int sys, int n_E, const double* E, int precision,
                double* resid, int* iters, int* status);
 
 /*
- * pwqt_solve for several systems (e.g. bias points of one device) at the same n_E
- * energies: results are system-major, entry s * n_E + e for system sys_ids[s];
- * node_n holds n_E * N_s * 2 values per system, systems back to back in the
- * order given.  Errors: as pwqt_solve (nothing is written past the first failing
- * system's block).
+ * pwqt_solve for several systems (e.g. bias points of one device, Sec. 4: the
+ * solve repeated for every applied potential) at the same n_E energies: results
+ * are system-major, entry s * n_E + e for system sys_ids[s]; node_n holds
+ * n_E * N_s * 2 values per system, systems back to back in the order given.
+ * When the systems share one node count (and, for PWQT_MIXED / PWQT_FP32, the
+ * sliced residual is selected) every (system, energy) pair runs in the same
+ * batched launches -- each job carries its own system's node blocks, and the
+ * self-energy cache serves every bias point whose leads sit at the same energy;
+ * otherwise system by system.  Errors: as pwqt_solve (in the system-by-system
+ * case nothing is written past the first failing system's block).
  */
 int pwqt_solve_multi(pwqt_ctx* ctx, int n_sys, const int* sys_ids, int n_E, const double* E, int precision,
                      double* T, double* R, double* T_ds, int* n_open, double* node_n,
@@ -511,6 +516,12 @@ int pwqt_server_wait(pwqt_server* srv, long long ticket, double timeout_s, int* 
    rank), and the largest admitted working-set sum; reset != 0 restarts them. */
 int pwqt_server_stats(pwqt_server* srv, long long* completed, double* p50_s, double* p99_s,
                       size_t* peak_admitted_bytes, int reset);
+
+/* Continuous batching since the last reset of pwqt_server_stats: batched solves
+   run, requests they held, and the largest batch.  Requests queued on one basis
+   with the same node count and precision share a batched solve (up to 8 distinct
+   potentials, within the budget); the paper has no counterpart. */
+int pwqt_server_batch_stats(pwqt_server* srv, long long* batches, long long* requests, long long* largest);
 
 /* Message of the last failure on this server (valid until the next failure). */
 const char* pwqt_server_last_error(pwqt_server* srv);

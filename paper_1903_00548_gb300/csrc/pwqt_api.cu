@@ -20,17 +20,58 @@ __global__ void k_bands_hk(int n, double2 ph, const double2* H0, const double2* 
     Mk[(size_t)c * n + r] = cadd(M0[rm], cadd(cmul(M1[rm], ph), cmul(cconj(M1[tm]), iph)));
 }
 
-int solve_common(pwqt_ctx* c, int sys, int n_E, const double* E, int precision, SolveOut& dev, cudaStream_t st,
-                 const DensityAcc* dens = nullptr) {
-    if (!c->n) return fail(c, PWQT_ERR_STATE, "no basis: call pwqt_assemble_intrinsic first");
-    auto it = c->systems.find(sys);
-    if (it == c->systems.end()) return fail(c, PWQT_ERR_STATE, "unknown system: call pwqt_set_extrinsic first");
+int check_solve_args(pwqt_ctx* c, int n_E, const double* E, int precision) {
     if (precision != PWQT_FP64 && precision != PWQT_MIXED && precision != PWQT_FP32)
         return fail(c, PWQT_ERR_INVALID_ARG, "bad precision");
     if (n_E < 0 || (n_E > 0 && !E)) return fail(c, PWQT_ERR_INVALID_ARG, "bad energies");
     if (c->n > 1024) return fail(c, PWQT_ERR_INVALID_ARG, "block size above 1024");
     for (int e = 0; e < n_E; ++e)
         if (!std::isfinite(E[e])) return fail(c, PWQT_ERR_INVALID_ARG, "non-finite energy");
+    return PWQT_OK;
+}
+
+// host output buffers of a solve (any may be NULL)
+struct HostOut {
+    double *T, *R, *T_ds;
+    int* n_open;
+    double *node_n, *resid;
+    int *iters, *status;
+};
+
+// device outputs for n_E results of N nodes, the solve `run` into them, copies to h
+template <class F>
+int solve_to_host(pwqt_ctx* c, int n_E, int N, const HostOut& h, F run) {
+    DBuf dT, dR, dTds, dno, dnn, dres, dit, dst;
+    size_t ne = (size_t)std::max(n_E, 1);
+    PWQT_TRY(alloc(c, dT, sizeof(double) * ne));
+    PWQT_TRY(alloc(c, dR, sizeof(double) * ne));
+    PWQT_TRY(alloc(c, dTds, sizeof(double) * ne));
+    PWQT_TRY(alloc(c, dno, sizeof(int) * 2 * ne));
+    PWQT_TRY(alloc(c, dnn, sizeof(double) * 2 * ne * std::max(N, 1)));
+    PWQT_TRY(alloc(c, dres, sizeof(double) * ne));
+    PWQT_TRY(alloc(c, dit, sizeof(int) * ne));
+    PWQT_TRY(alloc(c, dst, sizeof(int) * ne));
+    SolveOut o{dT.as<double>(), dR.as<double>(), dTds.as<double>(), dnn.as<double>(), dres.as<double>(),
+               dno.as<int>(), dit.as<int>(), dst.as<int>()};
+    PWQT_TRY(run(o));
+    PWQT_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (h.T) PWQT_CUDA(c, copy_sync(c, h.T, dT.p, sizeof(double) * n_E, cudaMemcpyDeviceToHost));
+    if (h.R) PWQT_CUDA(c, copy_sync(c, h.R, dR.p, sizeof(double) * n_E, cudaMemcpyDeviceToHost));
+    if (h.T_ds) PWQT_CUDA(c, copy_sync(c, h.T_ds, dTds.p, sizeof(double) * n_E, cudaMemcpyDeviceToHost));
+    if (h.n_open) PWQT_CUDA(c, copy_sync(c, h.n_open, dno.p, sizeof(int) * 2 * n_E, cudaMemcpyDeviceToHost));
+    if (h.node_n) PWQT_CUDA(c, copy_sync(c, h.node_n, dnn.p, sizeof(double) * 2 * n_E * N, cudaMemcpyDeviceToHost));
+    if (h.resid) PWQT_CUDA(c, copy_sync(c, h.resid, dres.p, sizeof(double) * n_E, cudaMemcpyDeviceToHost));
+    if (h.iters) PWQT_CUDA(c, copy_sync(c, h.iters, dit.p, sizeof(int) * n_E, cudaMemcpyDeviceToHost));
+    if (h.status) PWQT_CUDA(c, copy_sync(c, h.status, dst.p, sizeof(int) * n_E, cudaMemcpyDeviceToHost));
+    return PWQT_OK;
+}
+
+int solve_common(pwqt_ctx* c, int sys, int n_E, const double* E, int precision, SolveOut& dev, cudaStream_t st,
+                 const DensityAcc* dens = nullptr) {
+    if (!c->n) return fail(c, PWQT_ERR_STATE, "no basis: call pwqt_assemble_intrinsic first");
+    auto it = c->systems.find(sys);
+    if (it == c->systems.end()) return fail(c, PWQT_ERR_STATE, "unknown system: call pwqt_set_extrinsic first");
+    PWQT_TRY(check_solve_args(c, n_E, E, precision));
     return solve_batch(c, it->second, n_E, E, precision, dev, st, dens);
 }
 }  // namespace
@@ -153,31 +194,9 @@ int pwqt_solve(pwqt_ctx* c, int sys, int n_E, const double* E, int precision, do
     auto it = c->systems.find(sys);
     int N = it == c->systems.end() ? 0 : it->second.N;
     if (n_E == 0) return PWQT_OK;
-    DBuf dE, dT, dR, dTds, dno, dnn, dres, dit, dst;
-    size_t ne = (size_t)std::max(n_E, 1);
-    PWQT_TRY(alloc(c, dT, sizeof(double) * ne));
-    PWQT_TRY(alloc(c, dR, sizeof(double) * ne));
-    PWQT_TRY(alloc(c, dTds, sizeof(double) * ne));
-    PWQT_TRY(alloc(c, dno, sizeof(int) * 2 * ne));
-    PWQT_TRY(alloc(c, dnn, sizeof(double) * 2 * ne * std::max(N, 1)));
-    PWQT_TRY(alloc(c, dres, sizeof(double) * ne));
-    PWQT_TRY(alloc(c, dit, sizeof(int) * ne));
-    PWQT_TRY(alloc(c, dst, sizeof(int) * ne));
-    SolveOut o{dT.as<double>(), dR.as<double>(), dTds.as<double>(), dnn.as<double>(), dres.as<double>(),
-               dno.as<int>(), dit.as<int>(), dst.as<int>()};
-    PWQT_TRY(solve_common(c, sys, n_E, E, precision, o, c->stream));
-    PWQT_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (T) PWQT_CUDA(c, copy_sync(c, T, dT.p, sizeof(double) * n_E, cudaMemcpyDeviceToHost));
-    if (R) PWQT_CUDA(c, copy_sync(c, R, dR.p, sizeof(double) * n_E, cudaMemcpyDeviceToHost));
-    if (T_ds) PWQT_CUDA(c, copy_sync(c, T_ds, dTds.p, sizeof(double) * n_E, cudaMemcpyDeviceToHost));
-    if (n_open) PWQT_CUDA(c, copy_sync(c, n_open, dno.p, sizeof(int) * 2 * n_E, cudaMemcpyDeviceToHost));
-    if (node_n) PWQT_CUDA(c, copy_sync(c, node_n, dnn.p, sizeof(double) * 2 * n_E * N, cudaMemcpyDeviceToHost));
-    if (resid) PWQT_CUDA(c, copy_sync(c, resid, dres.p, sizeof(double) * n_E, cudaMemcpyDeviceToHost));
-    if (iters) PWQT_CUDA(c, copy_sync(c, iters, dit.p, sizeof(int) * n_E, cudaMemcpyDeviceToHost));
-    if (status) PWQT_CUDA(c, copy_sync(c, status, dst.p, sizeof(int) * n_E, cudaMemcpyDeviceToHost));
-    return PWQT_OK;
+    HostOut h{T, R, T_ds, n_open, node_n, resid, iters, status};
+    return solve_to_host(c, n_E, N, h, [&](SolveOut& o) { return solve_common(c, sys, n_E, E, precision, o, c->stream); });
 }
-
 int pwqt_solve_dev(pwqt_ctx* c, int sys, int n_E, const double* E, int precision, double* T, double* R, double* T_ds,
                    int* n_open, double* node_n, double* resid, int* iters, int* status, void* stream) {
     PWQT_TRY(check_ctx(c));
@@ -401,15 +420,38 @@ int pwqt_solve_multi(pwqt_ctx* c, int n_sys, const int* sys_ids, int n_E, const 
                      double* T_ds, int* n_open, double* node_n, double* resid, int* iters, int* status) {
     PWQT_TRY(check_ctx(c));
     if (n_sys < 0 || (n_sys > 0 && !sys_ids)) return fail(c, PWQT_ERR_INVALID_ARG, "bad system list");
-    size_t nn_off = 0;
+    if (!c->n) return fail(c, PWQT_ERR_STATE, "no basis: call pwqt_assemble_intrinsic first");
+    cudaSetDevice(c->dev);
+    std::vector<System*> sysq(n_sys);
+    bool same_N = true;
     for (int q = 0; q < n_sys; ++q) {
         auto it = c->systems.find(sys_ids[q]);
         if (it == c->systems.end()) return fail(c, PWQT_ERR_STATE, "unknown system in the list");
+        sysq[q] = &it->second;
+        same_N = same_N && sysq[q]->N == sysq[0]->N;
+    }
+    if (n_sys == 0 || n_E == 0) return PWQT_OK;
+    PWQT_TRY(check_solve_args(c, n_E, E, precision));
+    if (same_N && (precision == PWQT_FP64 || c->residual_kind == PWQT_RESIDUAL_SLICED)) {
+        // every (system, energy) pair in one batched solve, system-major: the bias points
+        // of a device share the launches (each job carries its own system's blocks)
+        const int tot = n_sys * n_E;
+        std::vector<double> Eall(tot);
+        std::vector<System*> of(tot);
+        for (int q = 0; q < n_sys; ++q)
+            for (int e = 0; e < n_E; ++e) { Eall[(size_t)q * n_E + e] = E[e]; of[(size_t)q * n_E + e] = sysq[q]; }
+        HostOut h{T, R, T_ds, n_open, node_n, resid, iters, status};
+        return solve_to_host(c, tot, sysq[0]->N, h, [&](SolveOut& o) {
+            return solve_batch(c, *sysq[0], tot, Eall.data(), precision, o, c->stream, nullptr, of.data());
+        });
+    }
+    size_t nn_off = 0;
+    for (int q = 0; q < n_sys; ++q) {
         const size_t o = (size_t)q * n_E;
         PWQT_TRY(pwqt_solve(c, sys_ids[q], n_E, E, precision, T ? T + o : nullptr, R ? R + o : nullptr, T_ds ? T_ds + o : nullptr,
                             n_open ? n_open + 2 * o : nullptr, node_n ? node_n + nn_off : nullptr, resid ? resid + o : nullptr,
                             iters ? iters + o : nullptr, status ? status + o : nullptr));
-        nn_off += (size_t)n_E * it->second.N * 2;
+        nn_off += (size_t)n_E * sysq[q]->N * 2;
     }
     return PWQT_OK;
 }

@@ -238,8 +238,11 @@ struct SolveOut {
     double *T, *R, *T_ds, *node_n, *resid;
     int *n_open, *iters, *status;
 };
+// sys_of[e] (optional): the system of energy e (bias points of one device, all with
+// s's node count) -- several systems in one batched launch; NULL: every energy is s's
 int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E_host, int precision,
-                const SolveOut& dev_out, cudaStream_t st, const DensityAcc* dens = nullptr);
+                const SolveOut& dev_out, cudaStream_t st, const DensityAcc* dens = nullptr,
+                System* const* sys_of = nullptr);
 
 // density (density.cu)
 int density_alloc(pwqt_ctx* c, System& s);

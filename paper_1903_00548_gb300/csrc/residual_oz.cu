@@ -304,7 +304,10 @@ __global__ void k_c_slice(const double2* __restrict__ C, long long sC, const int
 // ---------------------------------------------------------------- the slice-product GEMM
 __global__ void __launch_bounds__(THREADS, 1) k_oz_gemm(const GemmArgs G) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int ct = blockIdx.x, rt = blockIdx.y, z = blockIdx.z;
+    // column tile: launches over one energy (Sigma) or one system's energies (HV) start at
+    // the first tile of their column range
+    const int c_first = G.mode == MODE_SIGMA ? (int)blockIdx.z * G.m : G.col_lo;
+    const int ct = blockIdx.x + c_first / TN, rt = blockIdx.y, z = blockIdx.z;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n = G.n, N = G.N, m = G.m, n_pad = G.n_pad;
     const int RT = 2 * n_pad / TM, KC = 2 * n_pad / KCH;
@@ -327,6 +330,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_oz_gemm(const GemmArgs G) {
         const int c_lo = e_act * m, c_hi = c_lo + m;
         if (ct * TN >= c_hi || ct * TN + TN <= c_lo) return;
     } else {
+        if (ct >= G.nct || ct * TN >= G.col_hi || ct * TN + TN <= G.col_lo) return;
         node = z;
         nseg_tot = 3;
         s_lo = node == 0 ? 1 : 0;
@@ -459,7 +463,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_oz_gemm(const GemmArgs G) {
                 for (int j = 0; j < 16; ++j) {
                     const int col = ct * TN + half * 16 + j;
                     const int k = col / m, g = col % m;
-                    if (k >= G.n_act || (e_act >= 0 && k != e_act)) continue;
+                    if (k >= G.n_act || (e_act >= 0 && k != e_act) || col < G.col_lo || col >= G.col_hi) continue;
                     const int fe = G.fexp[col];
                     const int e = G.act[k];
                     const ResJob& J = G.jobs[e];
@@ -587,7 +591,12 @@ void slice_solution(const double2* C, long long sC, const int* act, int n_act, i
 
 void gemm(const GemmArgs& G, int items, cudaStream_t st) {
     const int n_pad = G.n_pad;
-    dim3 grid(G.nct, 2 * n_pad / TM, items);
+    int tiles = G.nct;
+    if (G.mode == MODE_SIGMA) tiles = std::min(G.nct, (G.m + TN - 1) / TN + 1);     // one energy's columns
+    else if (G.col_lo > 0 || G.col_hi < G.nct * TN)                                // one system's columns
+        tiles = std::min(G.nct, (std::min(G.col_hi, G.nct * TN) - 1) / TN - G.col_lo / TN + 1);
+    if (tiles <= 0 || items <= 0) return;
+    dim3 grid(tiles, 2 * n_pad / TM, items);
     k_oz_gemm<<<grid, THREADS, SMEM_BYTES, st>>>(G);
 }
 

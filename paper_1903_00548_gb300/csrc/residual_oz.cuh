@@ -44,6 +44,7 @@ struct GemmArgs {
     double2* R;                 // residual, per energy stride sC: [node][row][m]
     long long sC;
     int sigma_side;             // MODE_SIGMA: 0 source (node 0), 1 drain (node N-1); item = active energy
+    int col_lo, col_hi;         // MODE_M / MODE_HV: the columns this launch writes (one system's energies)
 };
 
 int padded(int n);                                  // n rounded up to a multiple of 64

@@ -2,13 +2,17 @@
 // queueing, admission and accounting logic is tested on its own.
 //
 // Requests carry a key (the catalog basis they run on) and an estimated device
-// working set in bytes.  Every key has one FIFO queue and one worker thread (the
-// executor of a key is not re-entrant: one library context per basis), so work of
-// different keys runs concurrently, work of one key in arrival order.  A request
-// starts only while the working sets of the requests running at that moment plus
-// its own stay within the byte budget (admission control); a request larger than
-// the whole budget is refused at submission.  Latency is measured from submission
-// to completion.
+// working set in bytes.  Every key has one queue and one worker thread (the executor
+// of a key is not re-entrant: one library context per basis), so work of different
+// keys runs concurrently.  When a worker takes the head of its queue it also takes
+// every later queued request that can share the head's batch (the merge predicate)
+// and fits, up to max_merge requests: they run as ONE batched execution (continuous
+// batching -- requests that arrived while the previous batch was on the device join
+// the next one as soon as it starts).  A batch starts only while the working sets of
+// the running batches plus its own stay within the byte budget (admission control);
+// a request larger than the whole budget is refused at submission.  Requests that
+// cannot merge keep their arrival order.  Latency is measured from submission to
+// completion.
 #pragma once
 
 #include <algorithm>
@@ -30,13 +34,17 @@ template <class Req>
 class Scheduler {
 public:
     using Clock = std::chrono::steady_clock;
-    // exec(key, request) runs one request on the key's worker thread and returns a status code
-    using Exec = std::function<int(int, Req&)>;
+    // exec(key, batch, rcs) runs a batch of requests on the key's worker thread and sets
+    // one status code per request
+    using Exec = std::function<void(int, std::vector<Req*>&, std::vector<int>&)>;
+    // merge(head, other): may `other` run in the same batch as `head`
+    using Merge = std::function<bool(const Req&, const Req&)>;
 
     enum : int { OK = 0, ERR_ARG = -1, ERR_STATE = -5, ERR_BUSY = -8, WAIT_TIMEOUT = 1 };
 
-    Scheduler(size_t budget_bytes, size_t queue_capacity, Exec exec)
-        : budget_(budget_bytes), capacity_(queue_capacity), exec_(std::move(exec)) {}
+    Scheduler(size_t budget_bytes, size_t queue_capacity, Exec exec, Merge merge = nullptr, size_t max_merge = 1)
+        : budget_(budget_bytes), capacity_(queue_capacity), exec_(std::move(exec)), merge_(std::move(merge)),
+          max_merge_(std::max<size_t>(1, max_merge)) {}
 
     ~Scheduler() { shutdown(); }
 
@@ -105,10 +113,19 @@ public:
         if (peak_bytes) *peak_bytes = peak_;
     }
 
+    // batches executed and the requests they held (requests / batches = mean batch size)
+    void batch_stats(long long* batches, long long* requests, long long* largest) {
+        std::lock_guard<std::mutex> g(m_);
+        if (batches) *batches = batches_;
+        if (requests) *requests = batched_;
+        if (largest) *largest = largest_;
+    }
+
     void reset_stats() {
         std::lock_guard<std::mutex> g(m_);
         latencies_.clear();
         peak_ = in_use_;
+        batches_ = batched_ = largest_ = 0;
     }
 
     // finish the queued work, then stop the workers
@@ -146,22 +163,44 @@ private:
                 return in_use_ + jobs_[L->queue.front()].bytes <= budget_;
             });
             if (L->queue.empty()) return;   // stopping and drained
-            const long long id = L->queue.front();
+            std::vector<long long> ids{L->queue.front()};
             L->queue.pop_front();
-            --queued_;
-            Job& j = jobs_[id];
-            in_use_ += j.bytes;
+            size_t bytes = jobs_[ids[0]].bytes;
+            // later requests that can share the head's batch and still fit join it
+            if (merge_)
+                for (auto it = L->queue.begin(); it != L->queue.end() && ids.size() < max_merge_;) {
+                    const Job& j = jobs_[*it];
+                    if (merge_(jobs_[ids[0]].req, j.req) && in_use_ + bytes + j.bytes <= budget_) {
+                        ids.push_back(*it);
+                        bytes += j.bytes;
+                        it = L->queue.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+            queued_ -= ids.size();
+            in_use_ += bytes;
             peak_ = std::max(peak_, in_use_);
-            Req req = j.req;
+            ++batches_;
+            batched_ += (long long)ids.size();
+            largest_ = std::max(largest_, (long long)ids.size());
+            std::vector<Req> reqs;
+            reqs.reserve(ids.size());
+            for (long long id : ids) reqs.push_back(jobs_[id].req);
             g.unlock();
-            const int rc = exec_(key, req);
+            std::vector<Req*> ptrs;
+            for (auto& r : reqs) ptrs.push_back(&r);
+            std::vector<int> rcs(ids.size(), 0);
+            exec_(key, ptrs, rcs);
             g.lock();
-            Job& jd = jobs_[id];
-            jd.rc = rc;
-            jd.done = true;
-            jd.latency = std::chrono::duration<double>(Clock::now() - jd.submitted).count();
-            latencies_.push_back(jd.latency);
-            in_use_ -= jd.bytes;
+            for (size_t q = 0; q < ids.size(); ++q) {
+                Job& jd = jobs_[ids[q]];
+                jd.rc = rcs[q];
+                jd.done = true;
+                jd.latency = std::chrono::duration<double>(Clock::now() - jd.submitted).count();
+                latencies_.push_back(jd.latency);
+            }
+            in_use_ -= bytes;
             cv_done_.notify_all();
             cv_work_.notify_all();
         }
@@ -169,6 +208,9 @@ private:
 
     const size_t budget_, capacity_;
     Exec exec_;
+    Merge merge_;
+    const size_t max_merge_;
+    long long batches_ = 0, batched_ = 0, largest_ = 0;
     std::mutex m_;
     std::condition_variable cv_work_, cv_done_;
     std::map<int, std::unique_ptr<Lane>> lanes_;

@@ -3,12 +3,17 @@
 // buffers) and collect them by ticket.  One library context per catalog basis keeps
 // its intrinsic blocks, contact self-energy cache and factor workspaces resident;
 // each context has its own CUDA stream and host worker thread, so requests on
-// different bases run on the device at the same time, requests on one basis in
-// arrival order.  Admission: a request starts only while the estimated working sets
-// of the running requests plus its own fit the server's device-memory budget
-// (scheduler.h).  Solves run exactly as pwqt_solve_dev would run them; the worker
-// reuses device output buffers and up to SLOTS potentials per basis, so steady-state
-// requests whose energies are already in the contact cache allocate nothing.
+// different bases run on the device at the same time.  Continuous batching: when a
+// basis' worker starts, every request queued on that basis with the same node count
+// and precision joins the batch (up to SLOTS distinct potentials and within the
+// budget), and the batch runs as ONE batched solve over all its (potential, energy)
+// pairs -- each job with its own potential's node blocks -- so requests that
+// arrived while the previous batch was on the device start together as soon as it
+// ends.  Admission: a batch starts only while the estimated working sets of the
+// running batches plus its own fit the server's device-memory budget
+// (scheduler.h).  The worker reuses device output buffers and up to SLOTS
+// potentials per basis, so steady-state requests whose energies are already in the
+// contact cache allocate nothing.
 #include <cmath>
 #include <cstring>
 #include <list>
@@ -19,6 +24,7 @@
 #include <vector>
 
 #include "pwqt_internal.cuh"
+#include "residual_oz.cuh"
 #include "scheduler.h"
 #include "sweep_mixed.cuh"
 
@@ -92,7 +98,9 @@ int slot_for(Lane& L, const SrvReq& r, int* sys) {
     return PWQT_OK;
 }
 
-int run_request(pwqt_server* s, int basis, SrvReq& r) {
+// One merged batch: the requests' potentials (slots), all their energies in one
+// batched solve, results scattered back to each request's host buffers.
+void run_batch(pwqt_server* s, int basis, std::vector<SrvReq*>& reqs, std::vector<int>& rcs) {
     Lane* Lp;
     {
         std::lock_guard<std::mutex> g(s->lanes_m);
@@ -100,12 +108,25 @@ int run_request(pwqt_server* s, int basis, SrvReq& r) {
     }
     Lane& L = *Lp;
     pwqt_ctx* c = L.ctx;
-    int sys = 0;
-    int rc = slot_for(L, r, &sys);
-    if (rc != PWQT_OK) return srv_fail(s, rc, std::string("request potential: ") + pwqt_last_error(c));
-    const size_t nE = r.E.size(), N = (size_t)r.N;
+    auto fail_all = [&](int rc, const std::string& msg) {
+        srv_fail(s, rc, msg);
+        for (auto& r : rcs) r = rc;
+    };
+    const int N = reqs[0]->N, precision = reqs[0]->precision;
+    std::vector<double> E;
+    std::vector<pwqt::System*> of;
+    std::vector<size_t> first(reqs.size() + 1, 0);
+    for (size_t q = 0; q < reqs.size(); ++q) {
+        int sys = 0;
+        const int rc = slot_for(L, *reqs[q], &sys);
+        if (rc != PWQT_OK) return fail_all(rc, std::string("request potential: ") + pwqt_last_error(c));
+        pwqt::System* sp = &c->systems.at(sys);
+        for (double e : reqs[q]->E) { E.push_back(e); of.push_back(sp); }
+        first[q + 1] = E.size();
+    }
+    const size_t nE = E.size(), NN = (size_t)N;
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t b_d = up(sizeof(double) * nE), b_nn = up(sizeof(double) * nE * N * 2), b_i = up(sizeof(int) * nE),
+    const size_t b_d = up(sizeof(double) * nE), b_nn = up(sizeof(double) * nE * NN * 2), b_i = up(sizeof(int) * nE),
                  b_no = up(sizeof(int) * nE * 2);
     const size_t need = 4 * b_d + b_nn + 2 * b_i + b_no;
     cudaSetDevice(c->dev);
@@ -115,35 +136,44 @@ int run_request(pwqt_server* s, int basis, SrvReq& r) {
         L.dev_bytes = 0;
         if (cudaMalloc(&L.dev, need) != cudaSuccess) {
             cudaGetLastError();
-            return srv_fail(s, PWQT_ERR_OOM, "device output buffers");
+            return fail_all(PWQT_ERR_OOM, "device output buffers");
         }
         L.dev_bytes = need;
     }
     char* p = static_cast<char*>(L.dev);
-    double* dT = (double*)p; p += b_d;
-    double* dR = (double*)p; p += b_d;
-    double* dTds = (double*)p; p += b_d;
-    double* dres = (double*)p; p += b_d;
-    double* dnn = (double*)p; p += b_nn;
-    int* dit = (int*)p; p += b_i;
-    int* dst = (int*)p; p += b_i;
-    int* dno = (int*)p;
-    rc = pwqt_solve_dev(c, sys, (int)nE, r.E.data(), r.precision, dT, dR, dTds, dno, dnn, dres, dit, dst, c->stream);
-    if (rc != PWQT_OK) return srv_fail(s, rc, std::string("solve: ") + pwqt_last_error(c));
-    auto back = [&](void* host, const void* devp, size_t bytes) {
-        if (host) cudaMemcpyAsync(host, devp, bytes, cudaMemcpyDeviceToHost, c->stream);
-    };
-    back(r.T, dT, sizeof(double) * nE);
-    back(r.R, dR, sizeof(double) * nE);
-    back(r.T_ds, dTds, sizeof(double) * nE);
-    back(r.resid, dres, sizeof(double) * nE);
-    back(r.node_n, dnn, sizeof(double) * nE * N * 2);
-    back(r.iters, dit, sizeof(int) * nE);
-    back(r.status, dst, sizeof(int) * nE);
-    back(r.n_open, dno, sizeof(int) * nE * 2);
+    pwqt::SolveOut o;
+    o.T = (double*)p; p += b_d;
+    o.R = (double*)p; p += b_d;
+    o.T_ds = (double*)p; p += b_d;
+    o.resid = (double*)p; p += b_d;
+    o.node_n = (double*)p; p += b_nn;
+    o.iters = (int*)p; p += b_i;
+    o.status = (int*)p; p += b_i;
+    o.n_open = (int*)p;
+    // one system: the plain batched solve; several: every (potential, energy) pair in the
+    // same launches (mixed precision needs the sliced residual for that)
+    bool several = false;
+    for (auto* sp : of) several = several || sp != of[0];
+    int rc = pwqt::solve_batch(c, *of[0], (int)nE, E.data(), precision, o, c->stream, nullptr, several ? of.data() : nullptr);
+    if (rc != PWQT_OK) return fail_all(rc, std::string("solve: ") + pwqt_last_error(c));
+    for (size_t q = 0; q < reqs.size(); ++q) {
+        SrvReq& r = *reqs[q];
+        const size_t e0 = first[q], ne = first[q + 1] - first[q];
+        auto back = [&](void* host, const void* devp, size_t bytes) {
+            if (host) cudaMemcpyAsync(host, devp, bytes, cudaMemcpyDeviceToHost, c->stream);
+        };
+        back(r.T, o.T + e0, sizeof(double) * ne);
+        back(r.R, o.R + e0, sizeof(double) * ne);
+        back(r.T_ds, o.T_ds + e0, sizeof(double) * ne);
+        back(r.resid, o.resid + e0, sizeof(double) * ne);
+        back(r.node_n, o.node_n + e0 * NN * 2, sizeof(double) * ne * NN * 2);
+        back(r.iters, o.iters + e0, sizeof(int) * ne);
+        back(r.status, o.status + e0, sizeof(int) * ne);
+        back(r.n_open, o.n_open + 2 * e0, sizeof(int) * ne * 2);
+    }
     const cudaError_t e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return srv_fail(s, PWQT_ERR_CUDA, std::string("copy back: ") + cudaGetErrorString(e));
-    return PWQT_OK;
+    if (e != cudaSuccess) return fail_all(PWQT_ERR_CUDA, std::string("copy back: ") + cudaGetErrorString(e));
+    for (auto& r : rcs) r = PWQT_OK;
 }
 
 // device working set of a request, as the solve would size it (the injected-mode
@@ -154,8 +184,14 @@ size_t estimate_bytes(const Lane& L, const SrvReq& r) {
     const size_t batch = std::min<size_t>(nE, L.ctx->opts.batch > 0 ? (size_t)L.ctx->opts.batch : nE);
     size_t per = r.precision == PWQT_FP64 ? sizeof(double2) * (N * n * (n + m) + n * n)
                                           : pwqt::mixed_bytes_per_energy((int)n, (int)N, (int)m);
-    return per * batch + 2 * sizeof(double2) * N * n * n;   // + the potential's node blocks
+    size_t panel = 0;   // the potential's slice panels of the tensor-core residual
+    if (r.precision != PWQT_FP64 && L.ctx->residual_kind == PWQT_RESIDUAL_SLICED)
+        panel = (N + 1) * pwqt::oz::panel_item_bytes((int)n, 3);
+    return per * batch + 2 * sizeof(double2) * N * n * n + panel;   // + the potential's node blocks
 }
+
+// requests that can share one batched solve: same node count and precision
+bool mergeable(const SrvReq& a, const SrvReq& b) { return a.N == b.N && a.precision == b.precision; }
 
 }  // namespace
 
@@ -177,8 +213,9 @@ int pwqt_server_create(pwqt_server** out, const pwqt_server_opts* o) {
     cudaMemGetInfo(&free_b, &total_b);
     s->budget = s->opts.hbm_budget_bytes ? s->opts.hbm_budget_bytes : (size_t)(0.7 * (double)free_b);
     const size_t cap = s->opts.queue_capacity > 0 ? (size_t)s->opts.queue_capacity : 4096;
-    s->sched = std::make_unique<pwqt::Scheduler<SrvReq>>(s->budget, cap,
-                                                        [s](int basis, SrvReq& r) { return run_request(s, basis, r); });
+    s->sched = std::make_unique<pwqt::Scheduler<SrvReq>>(
+        s->budget, cap, [s](int basis, std::vector<SrvReq*>& b, std::vector<int>& rcs) { run_batch(s, basis, b, rcs); },
+        mergeable, (size_t)SLOTS);
     *out = s;
     return PWQT_OK;
 }
@@ -257,6 +294,12 @@ int pwqt_server_stats(pwqt_server* s, long long* completed, double* p50_s, doubl
     if (!s) return PWQT_ERR_INVALID_ARG;
     s->sched->stats(completed, p50_s, p99_s, peak_admitted_bytes);
     if (reset) s->sched->reset_stats();
+    return PWQT_OK;
+}
+
+int pwqt_server_batch_stats(pwqt_server* s, long long* batches, long long* requests, long long* largest) {
+    if (!s) return PWQT_ERR_INVALID_ARG;
+    s->sched->batch_stats(batches, requests, largest);
     return PWQT_OK;
 }
 

@@ -105,9 +105,11 @@ __global__ void k_residual_fp64(SweepSys sys, const ResJob* __restrict__ jobs) {
     const double2* ci = J.C + (size_t)i * J.node_stride;
     const double2* cm1 = i > 0 ? J.C + (size_t)(i - 1) * J.node_stride : nullptr;
     const double2* cp1 = i < N - 1 ? J.C + (size_t)(i + 1) * J.node_stride : nullptr;
-    const double2* HV0 = sys.HV0 + (size_t)i * n * n;
-    const double2* HV1 = sys.HV1 + (size_t)i * n * n;
-    const double2* HVm = i > 0 ? sys.HV1 + (size_t)(i - 1) * n * n : nullptr;
+    const double2* HV0b = J.HV0 ? J.HV0 : sys.HV0;
+    const double2* HV1b = J.HV1 ? J.HV1 : sys.HV1;
+    const double2* HV0 = HV0b + (size_t)i * n * n;
+    const double2* HV1 = HV1b + (size_t)i * n * n;
+    const double2* HVm = i > 0 ? HV1b + (size_t)(i - 1) * n * n : nullptr;
     for (int t = threadIdx.x; t < n * m; t += blockDim.x) {
         int r = t / m, g = t % m;
         double2 acc = make_double2(0, 0);
@@ -165,19 +167,25 @@ __global__ void k_fill_int(int* p, int v, int cnt) {
 
 // ---------------------------------------------------------------- orchestration
 int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, const SolveOut& o, cudaStream_t st,
-                const DensityAcc* dens) {
+                const DensityAcc* dens, System* const* sys_of) {
     const int n = c->n, N = s.N;
     const size_t nn = (size_t)n * n;
+    auto sysE = [&](int e) -> System& { return sys_of ? *sys_of[e] : s; };
+    if (sys_of) {
+        if (dens) return fail(c, PWQT_ERR_INVALID_ARG, "density accumulation takes one system");
+        for (int e = 0; e < nE; ++e)
+            if (sys_of[e]->N != N) return fail(c, PWQT_ERR_INVALID_ARG, "a batch of several systems needs one node count");
+    }
     // 1. contact data (FP64 cache, computed on a miss)
     std::vector<LeadEntry*> ls(nE), ld(nE);
     {
         std::vector<double> keys;
-        for (int e = 0; e < nE; ++e) { keys.push_back(E[e] - s.Us); keys.push_back(E[e] - s.Ud); }
+        for (int e = 0; e < nE; ++e) { keys.push_back(E[e] - sysE(e).Us); keys.push_back(E[e] - sysE(e).Ud); }
         PWQT_TRY(fill_leads(c, keys));
     }
     for (int e = 0; e < nE; ++e) {
-        PWQT_TRY(lead_entry(c, E[e] - s.Us, &ls[e]));
-        PWQT_TRY(lead_entry(c, E[e] - s.Ud, &ld[e]));
+        PWQT_TRY(lead_entry(c, E[e] - sysE(e).Us, &ls[e]));
+        PWQT_TRY(lead_entry(c, E[e] - sysE(e).Ud, &ld[e]));
     }
     std::vector<int> ms(nE), md(nE), hst(nE);
     for (int e = 0; e < nE; ++e) {
@@ -188,7 +196,14 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
     }
     // 2. batches bounded by the device budget (after the mixed path's per-system slice
     // panels, which stay with the system)
-    if (precision != PWQT_FP64) PWQT_TRY(mixed_prepare(c, s, st));
+    if (precision != PWQT_FP64) {
+        PWQT_TRY(mixed_prepare(c, s, st));
+        if (sys_of) {
+            if (c->residual_kind != PWQT_RESIDUAL_SLICED)
+                return fail(c, PWQT_ERR_INVALID_ARG, "a batch of several systems needs the sliced residual");
+            for (int e = 0; e < nE; ++e) PWQT_TRY(mixed_prepare(c, *sys_of[e], st));
+        }
+    }
     size_t free_b = 0, total_b = 0;
     PWQT_CUDA(c, cudaMemGetInfo(&free_b, &total_b));
     size_t budget = c->opts.hbm_budget_bytes ? c->opts.hbm_budget_bytes : (size_t)(0.85 * (double)free_b);
@@ -236,6 +251,8 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
             J.E = E[e];
             J.ms = ms[e];
             J.md = md[e];
+            J.HV0 = sysE(e).HV0.as<double2>();
+            J.HV1 = sysE(e).HV1.as<double2>();
             const bool bad = (hst[e] & PWQT_ST_MODE_COUNT) != 0;
             J.sig_s = bad ? zero : Ls->sigma_s.as<double2>();
             J.sig_d = bad ? zero : Ld->sigma_d.as<double2>();
@@ -258,6 +275,7 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
             O.T = o.T + e; O.R = o.R + e; O.T_ds = o.T_ds + e; O.node_n = o.node_n + (size_t)e * N * 2;
             ResJob& Rj = res[b];
             Rj.E = E[e]; Rj.ms = ms[e]; Rj.md = md[e];
+            Rj.HV0 = J.HV0; Rj.HV1 = J.HV1;
             Rj.sig_s = J.sig_s; Rj.sig_d = J.sig_d; Rj.rhs_s = J.rhs_s; Rj.rhs_d = J.rhs_d;
             Rj.C = O.C; Rj.node_stride = O.node_stride; Rj.row_stride = O.row_stride;
             Rj.Rout = nullptr; Rj.r_node_stride = 0; Rj.r_row_stride = 0;
@@ -275,7 +293,7 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
         PWQT_CUDA(c, cudaMemcpyAsync(res_d.p, res.data(), sizeof(ResJob) * gn, cudaMemcpyHostToDevice, gs));
         if (precision != PWQT_FP64) {
             PWQT_TRY(solve_mixed(c, s, sys, jobs, jobs_d.as<SweepJob>(), res, res_d.as<ResJob>(), obs, obs_d.as<ObsJob>(), gn,
-                                 o.iters + g0, gs, precision == PWQT_MIXED, *L));
+                                 o.iters + g0, gs, precision == PWQT_MIXED, *L, sys_of ? sys_of + g0 : nullptr));
         } else {
             if (c->profile) PWQT_CUDA(c, cudaEventRecord(c->ev0, gs));
             launch_sweep_fp64(sys, jobs_d.as<SweepJob>(), gn, gs);

@@ -17,6 +17,8 @@ struct SweepSys {
 struct SweepJob {
     double E;
     int ms, md;                 // injected modes from source / drain (m = ms + md columns)
+    const double2* HV0;         // this energy's system blocks (several bias points in one
+    const double2* HV1;         // launch); NULL: the launch's SweepSys blocks
     const double2* sig_s;       // n x n
     const double2* sig_d;
     const double2* rhs_s;       // n x ms, row-major

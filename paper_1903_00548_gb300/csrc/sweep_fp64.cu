@@ -120,7 +120,7 @@ __device__ void green_backward(const SweepSys& sys, const SweepJob& J, double2* 
         for (int t = threadIdx.x; t < n * n; t += NT) R[(size_t)(t / n) * w + t % n] = make_double2(0, 0);
         __syncthreads();
         {
-            const double2* HV1 = sys.HV1 + (size_t)i * n * n;
+            const double2* HV1 = (J.HV1 ? J.HV1 : sys.HV1) + (size_t)i * n * n;
             const double2* M1 = sys.M1;
             auto A = [&](int r, int k) {                               // L_{i+1}[r][k] = conj(U_i[k][r])
                 size_t t = (size_t)k * n + r;
@@ -161,8 +161,8 @@ __global__ void __launch_bounds__(NT) k_sweep_fp64(SweepSys sys, const SweepJob*
     int st = 0;
     for (int i = 0; i < N; ++i) {
         double2* R = J.XY + (size_t)i * n * w;
-        const double2* HV0 = sys.HV0 + (size_t)i * n * n;
-        const double2* HV1 = sys.HV1 + (size_t)i * n * n;
+        const double2* HV0 = (J.HV0 ? J.HV0 : sys.HV0) + (size_t)i * n * n;
+        const double2* HV1 = (J.HV1 ? J.HV1 : sys.HV1) + (size_t)i * n * n;
         for (int t = threadIdx.x; t < n * n; t += NT) {
             double2 v = csub(cscale(sys.M0[t], E), HV0[t]);
             if (i == 0 && J.sig_s) v = csub(v, J.sig_s[t]);
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(NT) k_sweep_fp64(SweepSys sys, const SweepJob*
         __syncthreads();
         if (i > 0) {
             const double2* P = J.XY + (size_t)(i - 1) * n * w;   // [X_{i-1} | y_{i-1}]
-            const double2* HVp = sys.HV1 + (size_t)(i - 1) * n * n;
+            const double2* HVp = (J.HV1 ? J.HV1 : sys.HV1) + (size_t)(i - 1) * n * n;
             const double2* M1 = sys.M1;
             // L_i[r][k] = conj(U_{i-1}[k][r]), U_{i-1} = E M1 - HV1_{i-1}
             auto A = [&](int r, int k) {

@@ -63,9 +63,11 @@ __global__ void k_mx_form(MixSys S, int i, int only_L) {
     float2* F = S.F + e * S.sF + (size_t)i * n * n;
     float2* XY = S.XY + e * S.sXY + (size_t)i * n * w;
     float2* Lb = S.Lb + e * S.sL;
-    const double2* HV0 = S.HV0 + (size_t)i * n * n;
-    const double2* HV1 = S.HV1 + (size_t)i * n * n;
-    const double2* HVm = S.HV1 + (size_t)(i > 0 ? i - 1 : 0) * n * n;
+    const double2* HV0b = J.HV0 ? J.HV0 : S.HV0;
+    const double2* HV1b = J.HV1 ? J.HV1 : S.HV1;
+    const double2* HV0 = HV0b + (size_t)i * n * n;
+    const double2* HV1 = HV1b + (size_t)i * n * n;
+    const double2* HVm = HV1b + (size_t)(i > 0 ? i - 1 : 0) * n * n;
     const size_t nn = (size_t)n * n;
     if (only_L) {
         for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nn; t += (size_t)gridDim.x * blockDim.x) {
@@ -563,7 +565,7 @@ int mixed_prepare(pwqt_ctx* c, System& s, cudaStream_t st) {
 
 int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJob>& jobs, SweepJob* jobs_d, std::vector<ResJob>& res,
                 ResJob* res_d, std::vector<ObsJob>& obs, ObsJob* obs_d, int nb, int* iters_dev, cudaStream_t st, bool refine,
-                Lane& L) {
+                Lane& L, System* const* sys_of) {
     // idempotent (a function attribute of the device): set per call, no flag shared between host threads
     if (cgemm_tc_init() != 0) return fail(c, PWQT_ERR_CUDA, "tensor-core GEMM set-up failed");
     const int n = sys.n, N = sys.N;
@@ -718,6 +720,11 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         OG.jobs = res_d;
         OG.R = S.R64;
         OG.sC = S.sC;
+        OG.col_lo = 0;
+        OG.col_hi = 1 << 30;
+    } else if (sys_of) {
+        for (int b = 1; b < nb; ++b)
+            if (sys_of[b] != sys_of[0]) return fail(c, PWQT_ERR_INVALID_ARG, "a batch of several systems needs the sliced residual");
     }
     std::vector<int> act_h;
     auto residual = [&]() -> int {
@@ -746,10 +753,22 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
             OG.sigma_side = side;
             oz::gemm(OG, n_act, st);
         }
-        // r += (HV c): one panel item per node
-        OG.mode = oz::MODE_HV; OG.A = s.ozH.as<__nv_bfloat16>(); OG.a_item_bytes = oz::panel_item_bytes(n, 3);
-        OG.rexp = s.ozH_rexp.as<int>();
-        oz::gemm(OG, N, st);
+        // r += (HV c): one panel item per node, one launch per system over the columns
+        // of its energies (consecutive in the active list)
+        OG.mode = oz::MODE_HV; OG.a_item_bytes = oz::panel_item_bytes(n, 3);
+        for (int k0 = 0; k0 < n_act;) {
+            System& sk = sys_of ? *sys_of[act_h[k0]] : s;
+            int k1 = k0 + 1;
+            while (k1 < n_act && (sys_of ? sys_of[act_h[k1]] : &s) == &sk) ++k1;
+            OG.A = sk.ozH.as<__nv_bfloat16>();
+            OG.rexp = sk.ozH_rexp.as<int>();
+            OG.col_lo = k0 * m;
+            OG.col_hi = k1 * m;
+            oz::gemm(OG, N, st);
+            k0 = k1;
+        }
+        OG.col_lo = 0;
+        OG.col_hi = 1 << 30;
         if (c->profile) {
             PWQT_CUDA(c, cudaEventRecord(L.oz_ev[1], st));
             // work of these launches: the method's complex MACs (3N - 2 block products and

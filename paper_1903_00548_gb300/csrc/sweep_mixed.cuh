@@ -11,6 +11,8 @@ namespace pwqt {
 struct ResJob {
     double E;
     int ms, md;
+    const double2* HV0;        // this energy's system blocks; NULL: the launch's SweepSys blocks
+    const double2* HV1;
     const double2* sig_s;
     const double2* sig_d;
     const double2* rhs_s;
@@ -43,8 +45,10 @@ void launch_residual_finish(const ResJob* jobs, int nb, cudaStream_t st, const i
 size_t mixed_bytes_per_energy(int n, int N, int m);
 // slice panels of the tensor-core residual for the basis and system (once; kept)
 int mixed_prepare(pwqt_ctx* c, System& s, cudaStream_t st);
+// sys_of[b]: the system of energy b of the batch (all with the same node count), or
+// NULL when every energy belongs to s; several systems need the sliced residual
 int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJob>& jobs, SweepJob* jobs_d,
                 std::vector<ResJob>& res, ResJob* res_d, std::vector<ObsJob>& obs, ObsJob* obs_d, int nb, int* iters_dev,
-                cudaStream_t st, bool refine, Lane& lane);
+                cudaStream_t st, bool refine, Lane& lane, System* const* sys_of = nullptr);
 
 }  // namespace pwqt

@@ -30,7 +30,7 @@ EXPORTS = ["pwqt_create", "pwqt_destroy", "pwqt_last_error", "pwqt_assemble_intr
            "pwqt_density_reset", "pwqt_accumulate_density", "pwqt_get_density_matrix", "pwqt_density_grid",
            "pwqt_profile_refinement", "pwqt_set_refinement", "pwqt_set_residual", "pwqt_profile_residual", "pwqt_solve_multi",
            "pwqt_server_create", "pwqt_server_add_basis", "pwqt_server_submit", "pwqt_server_wait",
-           "pwqt_server_stats", "pwqt_server_last_error", "pwqt_server_destroy", "pwqt_integrate",
+           "pwqt_server_stats", "pwqt_server_batch_stats", "pwqt_server_last_error", "pwqt_server_destroy", "pwqt_integrate",
            "pwqt_transmission_caroli", "pwqt_self_consistent", "pwqt_green_diagonal"]
 
 
@@ -112,6 +112,7 @@ def load(path: str = LIB_PATH):
     lib.pwqt_server_submit.argtypes = [P, C.POINTER(RequestC), C.POINTER(C.c_longlong)]
     lib.pwqt_server_wait.argtypes = [P, C.c_longlong, D, ip, dp]
     lib.pwqt_server_stats.argtypes = [P, C.POINTER(C.c_longlong), dp, dp, C.POINTER(S), I]
+    lib.pwqt_server_batch_stats.argtypes = [P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
     lib.pwqt_server_last_error.argtypes = [P]
     lib.pwqt_server_last_error.restype = C.c_char_p
     lib.pwqt_server_destroy.argtypes = [P]
@@ -476,6 +477,12 @@ class Server:
         self._check(self.lib.pwqt_server_stats(self.h, C.byref(done), C.byref(p50), C.byref(p99), C.byref(peak),
                                                1 if reset else 0))
         return dict(completed=done.value, p50_s=p50.value, p99_s=p99.value, peak_admitted_bytes=peak.value)
+
+    def batch_stats(self):
+        """(batched solves, requests they held, largest batch) since the last stats reset."""
+        b, r, m = C.c_longlong(), C.c_longlong(), C.c_longlong()
+        self._check(self.lib.pwqt_server_batch_stats(self.h, C.byref(b), C.byref(r), C.byref(m)))
+        return b.value, r.value, m.value
 
     def close(self):
         if self.h:

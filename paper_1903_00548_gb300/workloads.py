@@ -215,3 +215,11 @@ def small_ribbon(n_bands: int = 16, n_nodes: int = 8, n_energies: int = 8,
     return Workload(f"ribbon_w{width}_n{2*n_bands}", cell, FormFactor(), gcut, n_bands,
                     n_nodes, midpoint_grid(0.0, 1.0, n_energies),
                     random_smooth(n_nodes, 0.3, 11), notes="small ribbon for tests")
+
+
+def bias_points(wl: Workload, n_bias: int = 8, step_eV: float = 0.05) -> list:
+    """Bias points of a workload (the batching configuration: energies x bias points):
+    node potentials U_q = U + a linear drop of V_q = q * step_eV (q < n_bias, 0..0.35 V
+    by default); the source lead stays at U(0), the drain lead sits at U(N) - V_q, so
+    every bias point needs its own drain self-energies at energy E + V_q."""
+    return [wl.U + linear_drop(wl.n_nodes, q * step_eV) for q in range(n_bias)]

@@ -3,7 +3,10 @@ potentials (more than the 8 kept per basis, so assembled potentials are evicted
 and rebuilt), all three precisions, submitted from two host threads at once.
 Every result must equal the same solve run alone on a separate context (FP64:
 1e-10 relative, the reductions' summation order aside; mixed: the 1e-8 bar of the
-refinement; complex64 alone: its own 1e-3 residual level)."""
+refinement; complex64 alone: its own 1e-3 residual level).  Continuous batching:
+same-basis requests queued behind a running batch (same node count and precision,
+different potentials and energies) run as one batched solve, and each result
+equals its standalone solve."""
 import threading
 
 import numpy as np
@@ -94,6 +97,33 @@ def test_server_results_equal_standalone_solves(pw):
             nn = np.max(np.abs(ref.node_n))
             assert np.max(np.abs(got.node_n - ref.node_n)) <= 1e-10 * nn, k
             assert np.all(got.status == ref.status), k
+    srv.close()
+
+
+def test_server_merges_queued_requests(pw):
+    cat = _catalog()
+    srv = pw.Server()
+    srv.add_basis(0, *cat[0])
+    # a long FP64 request holds the basis' worker while six mixed requests queue behind it
+    t_long = srv.submit(0, W.random_smooth(400, 0.2, 5), np.linspace(0.05, 1.5, 64), pw.FP64)
+    reqs = []
+    rng = np.random.default_rng(11)
+    for q in range(6):
+        U = W.random_smooth(16, 0.2, 500 + q)          # six potentials (the basis keeps eight)
+        E = np.sort(rng.uniform(0.2, 1.4, 2 + q % 3))
+        reqs.append((U, E, srv.submit(0, U, E, pw.MIXED)))
+    srv.wait(t_long)
+    got = [srv.wait(t)[0] for _, _, t in reqs]
+    batches, requests, largest = srv.batch_stats()
+    assert requests == 7 and largest >= 3 and batches < requests, (batches, requests, largest)
+    ctx = pw.Context()
+    ctx.assemble_intrinsic(*cat[0])
+    for (U, E, _), g in zip(reqs, got):
+        ctx.set_extrinsic(0, U)
+        ref = ctx.solve(0, E, pw.MIXED)
+        assert np.array_equal(g.n_open, ref.n_open)
+        assert np.all(np.abs(g.T - ref.T) <= 1e-8) and np.all(np.abs(g.R - ref.R) <= 1e-8), (g.T, ref.T)
+        assert np.all(g.status == ref.status)
     srv.close()
 
 
