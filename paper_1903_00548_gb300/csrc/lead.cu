@@ -200,6 +200,149 @@ __global__ void k_copy_col(double2* dst, const double2* src, int n) {
     if (r < n) dst[r] = src[r];
 }
 
+// Metric and flux forms of a set of traveling modes at one lambda = ph (|ph| = 1):
+// Gm[a][b] = c_a^H M(ph) c_b and F[a][b] = c_a^H V(ph) c_b with M(ph) = M1^H / ph + M0 +
+// ph M1 and the velocity form V(ph) = iL (ph K+ - K+^H / ph), K+ = H1 - Ec M1
+// (Eqs. hellmann-feynman, normalization).  Grid (g, g), one block per pair.
+__global__ void k_group_forms(int n, int g, const int* __restrict__ idx, double2 ph, double Ec, double L,
+                              const double2* __restrict__ H1, const double2* __restrict__ M0, const double2* __restrict__ M1,
+                              const double2* __restrict__ Cm, double2* Gm, double2* F) {
+    const int a = blockIdx.x, b = blockIdx.y;
+    const double2* ca = Cm + (size_t)idx[a] * n;
+    const double2* cb = Cm + (size_t)idx[b] * n;
+    const double2 iph = cconj(ph);
+    double2 sm = make_double2(0, 0), sf = make_double2(0, 0);
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        double2 mv = make_double2(0, 0), kv = make_double2(0, 0);   // (M(ph) c_b)_r, (ph K+ - K+^H/ph) c_b)_r
+        for (int k = 0; k < n; ++k) {
+            const double2 x = cb[k];
+            const size_t rk = (size_t)r * n + k, kr = (size_t)k * n + r;
+            const double2 m = cadd(M0[rk], cadd(cmul(ph, M1[rk]), cmul(iph, cconj(M1[kr]))));
+            const double2 kp = csub(H1[rk], cscale(M1[rk], Ec));
+            const double2 km = cconj(csub(H1[kr], cscale(M1[kr], Ec)));
+            cfma(mv, m, x);
+            cfma(kv, csub(cmul(ph, kp), cmul(iph, km)), x);
+        }
+        const double2 cr = cconj(ca[r]);
+        sm = cadd(sm, cmul(cr, mv));
+        sf = cadd(sf, cmul(cr, kv));
+    }
+    __shared__ double red[4][256];
+    red[0][threadIdx.x] = sm.x; red[1][threadIdx.x] = sm.y; red[2][threadIdx.x] = sf.x; red[3][threadIdx.x] = sf.y;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        Gm[a * g + b] = make_double2(red[0][0], red[1][0]);
+        // i L (c_a^H K c_b) with K = ph K+ - K+^H / ph
+        F[a * g + b] = make_double2(-L * red[3][0], L * red[2][0]);
+    }
+}
+
+// Generalised Hermitian eigenproblem F u = v Gm u of a small set (g <= 16, one
+// thread): Cholesky Gm = L L^H, Jacobi rotations on L^-1 F L^-H, U = L^-H W, so
+// that U^H Gm U = I and U^H F U = diag(v).  ok[0] = 0 when Gm is not positive definite.
+constexpr int GMAX = 16;
+__global__ void k_small_geig(int g, const double2* __restrict__ Gm_in, const double2* __restrict__ F_in, double2* U, double* vals,
+                             int* ok) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double2 Lc[GMAX][GMAX], A[GMAX][GMAX], W[GMAX][GMAX];
+    for (int i = 0; i < g; ++i)
+        for (int j = 0; j < g; ++j) { Lc[i][j] = make_double2(0, 0); A[i][j] = F_in[i * g + j]; W[i][j] = make_double2(i == j, 0); }
+    // Hermitian parts (the forms are Hermitian up to rounding)
+    for (int i = 0; i < g; ++i)
+        for (int j = i; j < g; ++j) {
+            const double2 x = cscale(cadd(A[i][j], cconj(A[j][i])), 0.5);
+            A[i][j] = x;
+            A[j][i] = cconj(x);
+        }
+    ok[0] = 1;
+    for (int j = 0; j < g; ++j) {
+        double d = 0.5 * (Gm_in[j * g + j].x + Gm_in[j * g + j].x);
+        for (int k = 0; k < j; ++k) d -= cnorm2(Lc[j][k]);
+        if (!(d > 0)) { ok[0] = 0; return; }
+        Lc[j][j] = make_double2(sqrt(d), 0);
+        for (int i = j + 1; i < g; ++i) {
+            double2 x = cscale(cadd(Gm_in[i * g + j], cconj(Gm_in[j * g + i])), 0.5);
+            for (int k = 0; k < j; ++k) x = csub(x, cmul(Lc[i][k], cconj(Lc[j][k])));
+            Lc[i][j] = cscale(x, 1.0 / Lc[j][j].x);
+        }
+    }
+    // A <- L^-1 A L^-H: forward substitution on the columns, then on the rows
+    for (int c = 0; c < g; ++c)
+        for (int i = 0; i < g; ++i) {
+            double2 x = A[i][c];
+            for (int k = 0; k < i; ++k) x = csub(x, cmul(Lc[i][k], A[k][c]));
+            A[i][c] = cscale(x, 1.0 / Lc[i][i].x);
+        }
+    for (int r = 0; r < g; ++r)
+        for (int j = 0; j < g; ++j) {
+            double2 x = A[r][j];
+            for (int k = 0; k < j; ++k) x = csub(x, cmul(A[r][k], cconj(Lc[j][k])));
+            A[r][j] = cscale(x, 1.0 / Lc[j][j].x);
+        }
+    // cyclic Jacobi: the rotation R = diag(1, e^{-i phi}) [[c, s], [-s, c]] zeroes A[p][q]
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        double off = 0, tot = 0;
+        for (int p = 0; p < g; ++p)
+            for (int q = 0; q < g; ++q) { tot += cnorm2(A[p][q]); if (p != q) off += cnorm2(A[p][q]); }
+        if (off <= 1e-30 * tot) break;
+        for (int p = 0; p < g; ++p)
+            for (int q = p + 1; q < g; ++q) {
+                const double b = sqrt(cnorm2(A[p][q]));
+                if (b == 0) continue;
+                const double2 e = cscale(A[p][q], 1.0 / b);         // e^{i phi}
+                const double2 ec = cconj(e);
+                const double tau = (A[q][q].x - A[p][p].x) / (2 * b);
+                const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1 + tau * tau));
+                const double cs = 1 / sqrt(1 + t * t), sn = t * cs;
+                // columns: X[:,p] = A[:,p] c - A[:,q] s e^{-i phi};  X[:,q] = A[:,p] s + A[:,q] c e^{-i phi}
+                for (int k = 0; k < g; ++k) {
+                    const double2 ap = A[k][p], aq = A[k][q];
+                    A[k][p] = csub(cscale(ap, cs), cscale(cmul(aq, ec), sn));
+                    A[k][q] = cadd(cscale(ap, sn), cscale(cmul(aq, ec), cs));
+                    const double2 wp = W[k][p], wq = W[k][q];
+                    W[k][p] = csub(cscale(wp, cs), cscale(cmul(wq, ec), sn));
+                    W[k][q] = cadd(cscale(wp, sn), cscale(cmul(wq, ec), cs));
+                }
+                // rows (R^H X): Y[p,:] = c X[p,:] - s e^{i phi} X[q,:];  Y[q,:] = s X[p,:] + c e^{i phi} X[q,:]
+                for (int k = 0; k < g; ++k) {
+                    const double2 xp = A[p][k], xq = A[q][k];
+                    A[p][k] = csub(cscale(xp, cs), cscale(cmul(xq, e), sn));
+                    A[q][k] = cadd(cscale(xp, sn), cscale(cmul(xq, e), cs));
+                }
+            }
+    }
+    // U = L^-H W (back substitution with L^H)
+    for (int c = 0; c < g; ++c)
+        for (int i = g - 1; i >= 0; --i) {
+            double2 x = W[i][c];
+            for (int k = i + 1; k < g; ++k) x = csub(x, cmul(cconj(Lc[k][i]), W[k][c]));
+            W[i][c] = cscale(x, 1.0 / Lc[i][i].x);
+        }
+    for (int i = 0; i < g; ++i) {
+        vals[i] = A[i][i].x;
+        for (int j = 0; j < g; ++j) U[i * g + j] = W[i][j];
+    }
+}
+
+// columns idx[0..g) of Cm <- scale * (those columns) U
+__global__ void k_apply_group(int n, int g, const int* __restrict__ idx, const double2* __restrict__ U, double scale, double2* Cm) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double2 x[GMAX], y[GMAX];
+    for (int a = 0; a < g; ++a) x[a] = Cm[(size_t)idx[a] * n + r];
+    for (int j = 0; j < g; ++j) {
+        double2 acc = make_double2(0, 0);
+        for (int a = 0; a < g; ++a) cfma(acc, x[a], U[a * g + j]);
+        y[j] = cscale(acc, scale);
+    }
+    for (int j = 0; j < g; ++j) Cm[(size_t)idx[j] * n + r] = y[j];
+}
+
 namespace {
 struct LinSolve {
     DBuf ipiv, info, work;
@@ -325,20 +468,85 @@ int compute_lead_shared(const pwqt_ctx* bz, pwqt_ctx* c, const LeadWorker& wk, d
         k_scale_col<<<(n + 127) / 128, b128, 0, st>>>(Cm.as<double2>(), n, j, scale);
         launches++;
     }
-    // two candidates refined onto the same mode: keep the first, reclassify the other by
-    // its raw |lambda|.  Distinct modes at the same lambda (a true degeneracy) are not
-    // flux-orthogonalised here: flag them.
-    for (int a = 0; a < n2; ++a)
-        for (int b = a + 1; b < n2; ++b)
-            if (trav[a] && trav[b] && std::hypot(hlam[a].x - hlam[b].x, hlam[a].y - hlam[b].y) < 1e-8) {
-                if (std::fabs(dEdk[a] - dEdk[b]) < 1e-8 * std::max(1.0, std::fabs(dEdk[a]))) {
-                    trav[b] = 0;
-                    hlam[b] = raw_lam[b];
+    // ---- traveling modes at one lambda (Sec. 3.1: degenerate modes must be made flux
+    // orthogonal, or the mode-resolved transmission picks up cross terms).  Within each
+    // set: the metric and flux forms Gm = C^H M(lambda) C, F = C^H V(lambda) C; two
+    // candidates whose normalised M-overlap is 1 are one mode found twice (the second is
+    // reclassified by its raw lambda); the rest are rotated by the generalised
+    // eigenvectors of (F, Gm) and normalised to c^H M c = L/2pi, their velocities the
+    // eigenvalues.  PWQT_ST_DEGENERATE marks an energy with such a set.
+    {
+        std::vector<char> seen(n2, 0);
+        for (int a = 0; a < n2; ++a) {
+            if (!trav[a] || seen[a]) continue;
+            std::vector<int> grp{a};
+            seen[a] = 1;
+            for (int b = a + 1; b < n2; ++b)
+                if (trav[b] && !seen[b] && std::hypot(hlam[a].x - hlam[b].x, hlam[a].y - hlam[b].y) < 1e-8) {
+                    grp.push_back(b);
+                    seen[b] = 1;
+                }
+            if (grp.size() < 2) continue;
+            if ((int)grp.size() > GMAX) { status |= PWQT_ST_DEGENERATE | PWQT_ST_NEAR_UNIT; continue; }
+            double2 lm = make_double2(0, 0);
+            for (int j : grp) lm = cadd(lm, hlam[j]);
+            lm = cscale(lm, 1.0 / std::hypot(lm.x, lm.y));
+            int g = (int)grp.size();
+            DBuf didx, dG, dF, dU, dv, dok;
+            PWQT_TRY(alloc(c, didx, sizeof(int) * g));
+            PWQT_TRY(alloc(c, dG, sizeof(double2) * g * g));
+            PWQT_TRY(alloc(c, dF, sizeof(double2) * g * g));
+            PWQT_CUDA(c, cudaMemcpyAsync(didx.p, grp.data(), sizeof(int) * g, cudaMemcpyHostToDevice, st));
+            k_group_forms<<<dim3(g, g), 256, 0, st>>>(n, g, didx.as<int>(), lm, Ec, L, bz->H1.as<double2>(), bz->M0.as<double2>(),
+                                                     bz->M1.as<double2>(), Cm.as<double2>(), dG.as<double2>(), dF.as<double2>());
+            launches++;
+            std::vector<double2> hG(g * g);
+            PWQT_CUDA(c, cudaMemcpyAsync(hG.data(), dG.p, sizeof(double2) * g * g, cudaMemcpyDeviceToHost, st));
+            PWQT_CUDA(c, cudaStreamSynchronize(st));
+            // one mode found twice: |c_a^H M c_b| = sqrt(c_a^H M c_a c_b^H M c_b)
+            std::vector<int> keep;
+            for (int q = 0; q < g; ++q) {
+                bool dup = false;
+                for (int p : keep) {
+                    const double2 x = hG[p * g + q];
+                    if (std::hypot(x.x, x.y) > (1.0 - 1e-6) * std::sqrt(hG[p * g + p].x * hG[q * g + q].x)) dup = true;
+                }
+                if (dup) {
+                    trav[grp[q]] = 0;
+                    hlam[grp[q]] = raw_lam[grp[q]];
                     status |= PWQT_ST_NEAR_UNIT;
                 } else {
-                    status |= PWQT_ST_DEGENERATE;
+                    keep.push_back(q);
                 }
             }
+            if (keep.size() < 2) continue;
+            std::vector<int> sub;
+            for (int q : keep) sub.push_back(grp[q]);
+            g = (int)sub.size();
+            PWQT_CUDA(c, cudaMemcpyAsync(didx.p, sub.data(), sizeof(int) * g, cudaMemcpyHostToDevice, st));
+            k_group_forms<<<dim3(g, g), 256, 0, st>>>(n, g, didx.as<int>(), lm, Ec, L, bz->H1.as<double2>(), bz->M0.as<double2>(),
+                                                     bz->M1.as<double2>(), Cm.as<double2>(), dG.as<double2>(), dF.as<double2>());
+            PWQT_TRY(alloc(c, dU, sizeof(double2) * g * g));
+            PWQT_TRY(alloc(c, dv, sizeof(double) * g));
+            PWQT_TRY(alloc(c, dok, sizeof(int)));
+            k_small_geig<<<1, 32, 0, st>>>(g, dG.as<double2>(), dF.as<double2>(), dU.as<double2>(), dv.as<double>(), dok.as<int>());
+            k_apply_group<<<(n + 127) / 128, 128, 0, st>>>(n, g, didx.as<int>(), dU.as<double2>(), std::sqrt(L / (2.0 * M_PI)),
+                                                          Cm.as<double2>());
+            launches += 3;
+            std::vector<double> hv(g);
+            int hok = 0;
+            PWQT_CUDA(c, cudaMemcpyAsync(hv.data(), dv.p, sizeof(double) * g, cudaMemcpyDeviceToHost, st));
+            PWQT_CUDA(c, cudaMemcpyAsync(&hok, dok.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+            PWQT_CUDA(c, cudaStreamSynchronize(st));
+            PWQT_CUDA(c, cudaGetLastError());
+            if (!hok) { status |= PWQT_ST_DEGENERATE | PWQT_ST_NEAR_UNIT; continue; }   // not resolved: flagged
+            for (int q = 0; q < g; ++q) {
+                hlam[sub[q]] = lm;
+                dEdk[sub[q]] = hv[q];
+            }
+            status |= PWQT_ST_DEGENERATE;
+        }
+    }
 
     // ---- classification (Sec. 3.1, drain convention lambda = c_{i+1}/c_i): a mode leaves
     // through the drain when it decays into it (|lambda| < 1) or travels with dE/dk > 0,
