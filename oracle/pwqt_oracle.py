@@ -362,16 +362,18 @@ def refine_traveling(blk, Ec: float, lam, c, iters: int = 8):
     return False, best[0], best[1]
 
 
-def lead_modes(blk, Ec: float, reciprocal: bool = False) -> LeadModes:
+def lead_modes(blk, Ec: float, reciprocal=False) -> LeadModes:
     """Complex band structure at energy Ec of the flat lead (Eqs. complex_bs and
     linearized_eigenvalue_symmetric): the 2n x 2n pencil
         [[K0, K-], [K+, 0]] [d; c] = lambda [[-K+, 0], [0, K+]] [d; c],  d = lambda c,
     K(E) = H - E M, solved by generalised QZ.  Traveling modes get their
     Hellmann-Feynman velocity (Eq. hellmann-feynman) and the normalisation
     c^H M(lambda) c = L/2pi (Eq. normalization); evanescent modes unit norm.
-    reciprocal=True solves the same pencil for mu = 1/lambda (QZ of (B, A)): the
-    same modes by a different rounding path, so that the spread of the results
-    measures the oracle's own rounding error."""
+    reciprocal=True solves the same pencil for mu = 1/lambda (QZ of (B, A)), and
+    reciprocal="cayley" the standard eigenproblem of its Cayley transform
+    (A + B)^-1 (A - B), mu = (lambda - 1)/(lambda + 1): the same modes by other
+    rounding paths, so that the spread of the results measures how well FP64
+    determines them (the oracle's own error bar, see error_bar)."""
     n, L = blk["n"], blk["L"]
     K0 = blk["H0"] - Ec * blk["M0"]
     Kp = blk["H1"] - Ec * blk["M1"]
@@ -379,7 +381,11 @@ def lead_modes(blk, Ec: float, reciprocal: bool = False) -> LeadModes:
     Z = np.zeros((n, n), complex)
     A = np.block([[K0, Km], [Kp, Z]])
     B = np.block([[-Kp, Z], [Z, Kp]])
-    if reciprocal:
+    if reciprocal == "cayley":
+        mu, V = sla.eig(np.linalg.solve(A + B, A - B))
+        with np.errstate(divide="ignore", invalid="ignore"):
+            lam = np.where(mu == 1, np.inf, (1.0 + mu) / (1.0 - mu))
+    elif reciprocal:
         mu, V = sla.eig(B, A)
         with np.errstate(divide="ignore", invalid="ignore"):
             lam = np.where(mu == 0, np.inf, 1.0 / mu)
@@ -565,7 +571,7 @@ class EnergyResult:
 def contacts_at(blk, E, Us, Ud, cache=None, allow_sort=False, reciprocal=False):
     """Source and drain contact data at energy E with flat leads at Us and Ud."""
     def modes(Ec):
-        key = ("reciprocal", Ec) if reciprocal else Ec
+        key = (str(reciprocal), Ec) if reciprocal else Ec
         if cache is not None and key in cache:
             return cache[key]
         m = lead_modes(blk, Ec, reciprocal)
@@ -655,11 +661,15 @@ def build_system(cell, ff, gcut, n_bands, U, nq=None, basis=None) -> System:
     return System(basis, elem, blk, np.asarray(U, float), Vd, Vu)
 
 
-def error_bar(r: EnergyResult, r_alt: EnergyResult) -> float:
+def error_bar(r: EnergyResult, *alts: EnergyResult) -> float:
     """The oracle's own rounding error at one energy, from what exact arithmetic
     fixes: total transmission is reciprocal (T_sd = T_ds for a real potential), and
-    the same modes from the reciprocal pencil give the same T, R, T_ds."""
-    return max(abs(r.T - r.T_ds), abs(r.T - r_alt.T), abs(r.T_ds - r_alt.T_ds), abs(r.R - r_alt.R))
+    the same modes from equivalent eigen-solves (the reciprocal pencil, the Cayley
+    transform; see lead_modes) give the same T, R, T_ds."""
+    bar = abs(r.T - r.T_ds)
+    for a in alts:
+        bar = max(bar, abs(r.T - a.T), abs(r.T_ds - a.T_ds), abs(r.R - a.R))
+    return bar
 
 
 def solve_workload(sys_: System, energies, cache=None):

@@ -49,17 +49,18 @@ def _oracle_results(sys_, energies):
     out = []
     for E in energies:
         r = O.solve_energy(sys_.blk, sys_.Vd, sys_.Vu, sys_.U, float(E), cache=cache)
-        alt = O.solve_energy(sys_.blk, sys_.Vd, sys_.Vu, sys_.U, float(E), cache=cache, reciprocal=True)
-        r.bar = O.error_bar(r, alt)
+        alts = [O.solve_energy(sys_.blk, sys_.Vd, sys_.Vu, sys_.U, float(E), cache=cache, reciprocal=k)
+                for k in (True, "cayley")]
+        r.bar = O.error_bar(r, *alts)
         out.append(r)
     return out
 
 
 def oracle_error(r):
     """The oracle's own error bar at this energy: total transmission is reciprocal
-    (T_sd = T_ds exactly for a real potential), and the reciprocal pencil gives the
-    same modes by another rounding path, so |T - T_ds| and the spread of the two
-    solves measure its rounding.  Where weakly evanescent modes (|lambda| ~ 0.96,
+    (T_sd = T_ds exactly for a real potential), and equivalent eigen-solves (the
+    reciprocal pencil, the Cayley transform) give the same modes by other rounding
+    paths, so |T - T_ds| and the spread of the three solves measure its rounding.  Where weakly evanescent modes (|lambda| ~ 0.96,
     from the basis near-null space) nearly coincide, the Bloch matrix B is
     ill-conditioned and this reaches ~1e-8 on the chain."""
     return r.bar

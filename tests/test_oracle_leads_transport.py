@@ -242,15 +242,17 @@ def test_reciprocal_pencil_gives_the_same_modes_and_transport():
     # the error-bar route of the oracle: QZ of the pencil for mu = 1/lambda must give the
     # same eigenvalues (to rounding) and, on the pristine chain, the same integer plateau
     s = chain_system()
-    for E in (0.3, 1.0):
-        a = O.lead_modes(s.blk, E)
-        b = O.lead_modes(s.blk, E, reciprocal=True)
-        fa = np.sort_complex(np.where(np.isfinite(a.lam), a.lam, 0))
-        fb = np.sort_complex(np.where(np.isfinite(b.lam), b.lam, 0))
-        small = np.abs(fa) < 1e6
-        assert np.allclose(fa[small], fb[small], rtol=1e-8, atol=1e-10)
-        assert a.traveling.sum() == b.traveling.sum()
-    sp = with_potential(s, np.zeros(20))
-    for E in (0.3, 0.9):
-        r = O.solve_energy(sp.blk, sp.Vd, sp.Vu, sp.U, E, reciprocal=True)
-        assert abs(r.T - 1.0) < 1e-9 and abs(r.R) < 1e-9
+    for kind in (True, "cayley"):
+        for E in (0.3, 1.0):
+            a = O.lead_modes(s.blk, E)
+            b = O.lead_modes(s.blk, E, reciprocal=kind)
+            # every finite eigenvalue has a partner in the other solve (nearest match)
+            fa = a.lam[np.isfinite(a.lam) & (np.abs(a.lam) < 1e6)]
+            fb = b.lam[np.isfinite(b.lam)]
+            d = np.min(np.abs(fa[:, None] - fb[None, :]), axis=1)
+            assert np.all(d <= 1e-7 * np.maximum(1.0, np.abs(fa))), (kind, d.max())
+            assert a.traveling.sum() == b.traveling.sum()
+        sp = with_potential(s, np.zeros(20))
+        for E in (0.3, 0.9):
+            r = O.solve_energy(sp.blk, sp.Vd, sp.Vu, sp.U, E, reciprocal=kind)
+            assert abs(r.T - 1.0) < 1e-9 and abs(r.R) < 1e-9
