@@ -632,11 +632,15 @@ def run_serving(args, world, rank, local):
         bad += int(np.count_nonzero(res.status & ~(pw.ST_NEAR_UNIT | pw.ST_DEGENERATE)))
     t_open = time.perf_counter() - t0
     st = srv.stats()
+    nbatch, nreq, largest = srv.batch_stats()
     srv.close()
     line = {"metric": "serving: energy-solves/s and p50/p99 request latency (mixed catalog)", "value": solves / t_open,
             "unit": "energy-solves/s", "n_gpus": 1, "higher_is_better": True, "impl": "ours",
             "latency_s": {"p50": st["p50_s"], "p99": st["p99_s"]}, "capacity_solves_per_s": cap,
             "arrival_rate_req_per_s": 0.7 * req_rate, "requests": n_req, "bad_status": bad, "setup_s": t_setup,
+            "continuous_batching": {"batched_solves": nbatch, "requests": nreq, "largest_batch": largest,
+                                    "rule": "queued requests of one basis with the same node count and precision "
+                                            "share the next batched solve (up to 8 potentials, within the budget)"},
             "data": "synthetic",
             "config": {"workload": "serving", "structure": "13 nm armchair ribbon, G_cut 30 nm^-1",
                        "catalog_block_sizes": sorted(cat), "nodes": "U[50,200]",
@@ -664,7 +668,7 @@ def main(argv=None):
     ap.add_argument("--serving", action="store_true", help="measure the serving loop instead of the headline metric")
     ap.add_argument("--batching", action="store_true",
                     help="measure energies x bias points in one batched solve instead of the headline metric")
-    ap.add_argument("--batching-workload", default="ribbon256")
+    ap.add_argument("--batching-workload", default="ribbon256_wide")
     ap.add_argument("--bias-points", type=int, default=8)
     ap.add_argument("--requests", type=int, default=60, help="requests per serving pass")
     ap.add_argument("--clocks-csv", default="/tmp/pwqt_clocks_{rank}.csv",

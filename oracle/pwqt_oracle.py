@@ -346,10 +346,18 @@ def refine_traveling(blk, Ec: float, lam, c, iters: int = 8):
         Mk = _m_lambda(blk, ph)
         Hk, Mk = 0.5 * (Hk + Hk.conj().T), 0.5 * (Mk + Mk.conj().T)
         w, V = sla.eigh(Hk, Mk)
-        # the band whose eigenvector overlaps most with the current mode
+        # the band whose eigenvector overlaps most with the current mode; when that band
+        # is degenerate at k, the mode is projected onto the whole eigenspace (M-orthogonal
+        # projection with the M-orthonormal eigenvectors of eigh), so that candidates of one
+        # degenerate set stay distinct for the flux orthogonalisation of Sec. 3.1
         ov = np.abs(V.conj().T @ (Mk @ c))
         b = int(np.argmax(ov / np.sqrt(np.abs(np.einsum("ij,ij->j", V.conj(), Mk @ V)))))
-        c = V[:, b] * (np.vdot(V[:, b], c) / abs(np.vdot(V[:, b], c)))
+        deg = np.flatnonzero(np.abs(w - w[b]) <= 1e-9 * max(1.0, abs(w[b])))
+        if len(deg) > 1:
+            Vd = V[:, deg]
+            c = Vd @ (Vd.conj().T @ (Mk @ c))
+        else:
+            c = V[:, b] * (np.vdot(V[:, b], c) / abs(np.vdot(V[:, b], c)))
         # dE/dk of that band at k (Eq. hellmann-feynman with E = w[b])
         Kb = blk["H1"] - w[b] * blk["M1"]
         slope = (np.vdot(c, _velocity_form(Kb, Kb.conj().T, ph, L) @ c) / np.vdot(c, Mk @ c)).real

@@ -16,6 +16,7 @@
 //   residual_oz.cu), A d = r with the stored complex64 factors, c += d.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 
 #include "cgemm_tc.cuh"
 #include "residual_oz.cuh"
@@ -334,51 +335,62 @@ __device__ __forceinline__ float2 shfl2(float2 v, int src) {
     return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
-constexpr int LR = 64;   // factor rows staged per chunk of the off-diagonal updates
+constexpr int LR = 64;    // factor rows staged per chunk of the off-diagonal updates
+constexpr int LDS = 34;   // padded row of a staged chunk (272 B: 16-byte aligned rows, conflict-free reads)
+constexpr int NSTG = 4;   // chunks in flight per CTA
 
 size_t lusolve_smem(int n) {
-    return ((n * sizeof(int) + 15) / 16) * 16 + sizeof(float2) * (PW * (PW + 1) + (size_t)LR * (PW + 1) + (size_t)n * LC);
+    return ((n * sizeof(int) + 15) / 16) * 16 + sizeof(float2) * (PW * (PW + 1) + (size_t)NSTG * LR * LDS + (size_t)n * LC);
 }
 
-// T[r][:] -= F[r][kb .. kb+wd) T[kb .. kb+wd)[:] for rows r in [r_begin, r_end), staged LR rows at a time
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int bytes) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(d), "l"(gmem), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+// T[r][:] -= F[r][kb .. kb+wd) T[kb .. kb+wd)[:] for rows r in [r_begin, r_end).  One CTA per
+// (energy, column group) streams about n^2 / 2 factor elements per triangle through L2, so
+// the chunks (LR rows x 32 columns, one 16-byte cp.async per two elements, rows and
+// columns past the factor zero-filled) are fetched NSTG - 1 ahead into a shared-memory ring.
 __device__ __forceinline__ void lu_offdiag(const float2* __restrict__ F, int n, int kb, int wd, int r_begin, int r_end,
                                            float2* Fs, float2* T) {
     const int t = threadIdx.x;
-    constexpr int PER = LR * PW / NT;
-    // one CTA per (energy, column group) leaves little to hide memory latency: the loads of
-    // the next chunk are issued into registers before this chunk's arithmetic, so they are
-    // in flight while it runs
-    float2 v[PER];
-    auto load = [&](int rc) {
-        const int rows = min(LR, r_end - rc);
-#pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            const int q = t + u * NT, rr = q / PW, l = q % PW;
-            v[u] = (rr < rows && l < wd) ? F[(size_t)(rc + rr) * n + kb + l] : make_float2(0.f, 0.f);
+    const int nch = (r_end - r_begin + LR - 1) / LR;
+    auto fetch = [&](int ch) {
+        if (ch < nch) {
+            float2* dst = Fs + (size_t)(ch % NSTG) * LR * LDS;
+            const int rc = r_begin + ch * LR;
+            for (int q = t; q < LR * (PW / 2); q += NT) {     // 16-byte pieces: row rr, columns 2l, 2l + 1
+                const int rr = q / (PW / 2), l2 = 2 * (q % (PW / 2));
+                const bool in = rc + rr < r_end && l2 < wd;
+                const float2* src = in ? F + (size_t)(rc + rr) * n + kb + l2 : F;
+                cp_async16(dst + rr * LDS + l2, src, in ? (l2 + 1 < wd ? 16 : 8) : 0);
+            }
         }
+        cp_async_commit();   // an empty group past the end keeps the wait count uniform
     };
-    if (r_begin < r_end) load(r_begin);
-    for (int rc = r_begin; rc < r_end; rc += LR) {
-        const int rows = min(LR, r_end - rc);
-#pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            const int q = t + u * NT;
-            Fs[(q / PW) * (PW + 1) + q % PW] = v[u];
-        }
-        __syncthreads();
-        if (rc + LR < r_end) load(rc + LR);
+    for (int ch = 0; ch < NSTG - 1; ++ch) fetch(ch);
+    for (int ch = 0; ch < nch; ++ch) {
+        cp_async_wait<NSTG - 2>();
+        __syncthreads();                    // chunk ch landed for every thread; chunk ch - 1 consumed
+        fetch(ch + NSTG - 1);
+        const float2* Fc = Fs + (size_t)(ch % NSTG) * LR * LDS;
+        const int rc = r_begin + ch * LR, rows = min(LR, r_end - rc);
         for (int q = t; q < rows * LC; q += NT) {
             const int rr = q / LC, g = q % LC;
             float2 a = T[(rc + rr) * LC + g];
 #pragma unroll 8
             for (int l = 0; l < wd; ++l) {   // rows kb + l < n of T only
-                const float2 L = Fs[rr * (PW + 1) + l];
+                const float2 L = Fc[rr * LDS + l];
                 ffma(a, make_float2(-L.x, -L.y), T[(kb + l) * LC + g]);
             }
             T[(rc + rr) * LC + g] = a;
         }
-        __syncthreads();
     }
+    cp_async_wait<0>();
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(NT) k_mx_lusolve(MixSys S, int i, const int* __restrict__ active) {
@@ -391,8 +403,8 @@ __global__ void __launch_bounds__(NT) k_mx_lusolve(MixSys S, int i, const int* _
     extern __shared__ unsigned char sm[];
     int* perm = reinterpret_cast<int*>(sm);                                              // n
     float2* Ld = reinterpret_cast<float2*>(sm + ((n * sizeof(int) + 15) / 16) * 16);     // PW x (PW+1)
-    float2* Fs = Ld + PW * (PW + 1);                                                     // LR x (PW+1)
-    float2* T = Fs + LR * (PW + 1);                                                      // n x LC
+    float2* Fs = Ld + PW * (PW + 1);                                                     // NSTG x LR x LDS
+    float2* T = Fs + NSTG * LR * LDS;                                                    // n x LC
     const float2* F = S.F + e * S.sF + (size_t)i * n * n;
     const int* pg = S.piv + e * S.sP + (size_t)i * n;        // row permutation (k_mx_perm)
     float2* W = S.XY + e * S.sXY + (size_t)i * n * w + n;     // row stride w

@@ -202,6 +202,18 @@ def ribbon512(n_nodes: int = 200, n_energies: int = 1024) -> Workload:
                     notes="armchair ribbon 13 nm, block 512, random smooth U <= 0.3 eV")
 
 
+def ribbon256_wide(n_nodes: int = 200, n_energies: int = 1024) -> Workload:
+    """Block 256 on the 13 nm ribbon (128 Bloch waves at Gamma and at Z, G_cut = 30
+    nm^-1), 200 nodes, the block-512 workload's energy window and potential.  The
+    batching configuration (energies x bias points, mixed precision) runs here: on the
+    1.5 nm ribbon the block-256 basis is too redundant for complex64 factors to refine
+    (M(k) eigenvalue ratio 4e-7; refinement stalls above 1e-6)."""
+    wl = ribbon512(n_nodes, n_energies)
+    wl.name, wl.n_bands = "ribbon256_wide", 128
+    wl.notes = "armchair ribbon 13 nm, block 256, random smooth U <= 0.3 eV"
+    return wl
+
+
 def ribbon512_narrow(n_nodes: int = 200, n_energies: int = 1024) -> Workload:
     """The 1.5 nm ribbon at G_cut = 60 nm^-1 with 256 bands per k-point (block 512):
     kept to document the numerically redundant basis (not a benchmark workload)."""

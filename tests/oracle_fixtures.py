@@ -39,3 +39,21 @@ def open_channels_from_bands(blk, E, nk=4001):
         s = np.sign(e)
         cnt += int(np.sum((s[:-1] < 0) & (s[1:] >= 0)))
     return cnt
+
+
+def symmetric_empty_lattice(U, Lz=0.4, Lx=0.5):
+    """A 2D cell without crystal potential and a Bloch basis symmetric under x -> -x:
+    plane waves with G_x in {0, +b_x, -b_x} (G_z = 0) at Gamma and at Z, so every +b_x
+    channel has a -b_x partner at the same lambda and with the same velocity (degenerate
+    traveling modes, Sec. 3.1).  Returns (cell, oracle system with node potentials U)."""
+    cell = W.Cell(dim=2, Lz=Lz, Lx=Lx, atoms=np.array([[0.0, 0.0]]), omega0=Lx * Lz)
+    bx = 2 * math.pi / Lx
+    mx, mz = np.array([0, 1, -1]), np.array([0, 0, 0])
+    groups, eps, kz = [], [], []
+    for k in (0.0, math.pi / Lz):
+        e = O.HB2M * ((mx * bx) ** 2 + k ** 2)
+        groups.append(dict(k=k, mx=mx, mz=mz, C=np.eye(3, dtype=complex), eps=e))
+        eps.append(e)
+        kz.append(np.full(3, k))
+    basis = O.basis_from_coefficients(cell, np.concatenate(eps), np.concatenate(kz), groups)
+    return cell, O.build_system(cell, W.FormFactor(v0=0.0), 0.0, 3, U, basis=basis)

@@ -9,31 +9,13 @@ multiplicity (3 above the +-b_x band bottom, 1 below), per-mode T_gamma = 1; wit
 potential: T, R, T_ds against the oracle (which flux-orthogonalises by
 diagonalising the velocity form) within 1e-9 relative or four times its own error
 bar.  The energies with degenerate sets carry PWQT_ST_DEGENERATE."""
-import math
-
 import numpy as np
 import pytest
 
-from oracle import pwqt_oracle as O
 from paper_1903_00548_gb300 import workloads as W
+from tests.oracle_fixtures import symmetric_empty_lattice
 
 pytestmark = pytest.mark.gpu
-
-LZ, LX = 0.4, 0.5
-
-
-def symmetric_empty_lattice(U):
-    cell = W.Cell(dim=2, Lz=LZ, Lx=LX, atoms=np.array([[0.0, 0.0]]), omega0=LX * LZ)
-    bx = 2 * math.pi / LX
-    mx, mz = np.array([0, 1, -1]), np.array([0, 0, 0])
-    groups, eps, kz = [], [], []
-    for k in (0.0, math.pi / LZ):
-        e = O.HB2M * ((mx * bx) ** 2 + k ** 2)
-        groups.append(dict(k=k, mx=mx, mz=mz, C=np.eye(3, dtype=complex), eps=e))
-        eps.append(e)
-        kz.append(np.full(3, k))
-    basis = O.basis_from_coefficients(cell, np.concatenate(eps), np.concatenate(kz), groups)
-    return cell, O.build_system(cell, W.FormFactor(v0=0.0), 0.0, 3, U, basis=basis)
 
 
 @pytest.fixture(scope="module")

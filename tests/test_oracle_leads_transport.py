@@ -8,7 +8,7 @@ import pytest
 from oracle import pwqt_oracle as O
 from paper_1903_00548_gb300 import workloads as W
 from tests.oracle_fixtures import (chain_system, open_channels_from_bands, small_ribbon_system,
-                                   with_potential)
+                                   symmetric_empty_lattice, with_potential)
 
 
 def _reconstruction_error(s):
@@ -256,3 +256,21 @@ def test_reciprocal_pencil_gives_the_same_modes_and_transport():
         for E in (0.3, 0.9):
             r = O.solve_energy(sp.blk, sp.Vd, sp.Vu, sp.U, E, reciprocal=kind)
             assert abs(r.T - 1.0) < 1e-9 and abs(r.R) < 1e-9
+
+
+def test_degenerate_traveling_pairs():
+    # mirror-symmetric empty-lattice cell: the +-b_x channels are degenerate pairs with
+    # equal velocities (Sec. 3.1).  Pristine: integer plateaus 1 / 3 with every mode fully
+    # transmitted; with a potential: flux conservation per injected mode and reciprocity
+    cell, s = symmetric_empty_lattice(np.zeros(6))
+    for E, n_open in ((1.0, 1), (6.5, 3), (7.5, 3), (9.0, 3)):
+        lm = O.lead_modes(s.blk, E)
+        assert lm.n_degenerate_sets == (2 if n_open == 3 else 0)
+        r = O.solve_energy(s.blk, s.Vd, s.Vu, s.U, E)
+        assert r.n_open_s == n_open and abs(r.T - n_open) < 1e-9 and np.all(np.abs(r.T_modes - 1) < 1e-9)
+    cell, s = symmetric_empty_lattice(W.random_smooth(8, 0.4, 21))
+    for E in (6.4, 7.1, 8.2, 9.3):
+        r = O.solve_energy(s.blk, s.Vd, s.Vu, s.U, E)
+        assert r.n_open_s == 3
+        assert np.max(np.abs(r.T_modes + r.R_modes - 1.0)) < 1e-9
+        assert abs(r.T - r.T_ds) < 1e-9
