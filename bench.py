@@ -408,6 +408,15 @@ def run_ours(args, world, rank, local):
                 "ms": ms64, "clocks": clk64, "status_nonzero": int(np.count_nonzero(st64 & 7)),
                 "max_abs_dT_mixed_vs_fp64": float(np.max(dT)), "mean_abs_dT_mixed_vs_fp64": float(np.mean(dT))}
 
+    # ---- a short serving pass (continuous batching; p50/p99 latency), on its own contexts
+    serving = None
+    if rank == 0 and not args.no_serving:
+        ctx.close()
+        torch.cuda.empty_cache()
+        clk_srv = Clocks(local, args.clocks_csv.format(rank=f"{rank}_serving"))
+        serving = serving_pass(local, args.serving_requests, blocks=(64, 128, 256))
+        serving["clocks"] = clk_srv.stop()
+
     # ---- rooflines (algorithmic work; peaks from MEASURED_PEAKS.json)
     bf16, hbm, src = peaks()
     tf32 = bf16 * NOMINAL_TFLOPS["tf32"] / NOMINAL_TFLOPS["bf16"]
@@ -452,7 +461,7 @@ def run_ours(args, world, rank, local):
                        f"(factor panels {N * n * n * 8 * batch / 1e9:.0f} GB per step)"},
             "latency_ms": {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99)),
                            "unit": f"per step of {batch} energies"},
-            "fp64_arm": fp64,
+            "fp64_arm": fp64, "serving": serving,
             "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
             "sigma_cold_s_per_energy": t_leads / max(1, len(E_all)), "setup_s": t_setup,
             "gpu_launches": int(launches), "clocks": clk_info, "roofline": roof, "roofline_sweep": roof_sweep,
@@ -486,7 +495,8 @@ def run_ours(args, world, rank, local):
                                     "sample": "failed: " + out[0].get("error", "?")}
     if rank == 0:
         print(json.dumps(line))
-    ctx.close()
+    if serving is None:
+        ctx.close()
     return 0
 
 
@@ -552,26 +562,21 @@ def run_batching(args, world, rank, local):
 
 
 # ----------------------------------------------------------------------------- serving
-def run_serving(args, world, rank, local):
-    """Serving loop: a catalog of bases (block 64..512), requests with a random basis,
-    device length, energy count and precision, first submitted all at once (capacity),
-    then with Poisson arrivals at 70 % of that capacity (latency).  Energies come from
-    a fixed 48-point grid per basis whose contact self-energies are computed before
-    timing, as a serving deployment keeps them resident."""
-    import torch
-    from paper_1903_00548_gb300 import build as B
+def serving_pass(local, n_req, blocks=(64, 128, 256, 512), seed=7):
+    """Serving loop: a catalog of bases (the 13 nm ribbon at the given block sizes),
+    requests with a random basis, device length, energy count and precision, first
+    submitted all at once (capacity), then with Poisson arrivals at 70 % of that rate
+    (latency).  Energies come from a fixed 48-point grid per basis whose contact
+    self-energies are computed before timing, as a serving deployment keeps them
+    resident.  Returns the measurements as a dict."""
     from paper_1903_00548_gb300 import pwqt as pw
     from paper_1903_00548_gb300 import workloads as W
 
-    B.build()
-    if rank != 0:
-        return 0
-    torch.cuda.set_device(local)
-    # one structure (the 13 nm ribbon, whose Bloch basis stays well conditioned) at four
-    # block sizes; energy windows inside each basis' band range (top Gamma/Z bands:
-    # 1.0/1.4 eV at 32 bands, 7.0/3.1 eV at 64, 8.9/9.5 eV at 128)
+    # one structure (the 13 nm ribbon, whose Bloch basis stays well conditioned); energy
+    # windows inside each basis' band range (top Gamma/Z bands: 1.0/1.4 eV at 32 bands,
+    # 7.0/3.1 eV at 64, 8.9/9.5 eV at 128)
     wl512 = W.ribbon512()
-    cat = {2 * b: (wl512.cell, wl512.ff, wl512.gcut, b) for b in (32, 64, 128, 256)}
+    cat = {nb: (wl512.cell, wl512.ff, wl512.gcut, nb // 2) for nb in blocks}
     e64 = W.RIBBON13_G30_E64
     grids = {64: np.linspace(0.0, 0.9, 48), 128: np.linspace(1.5, 2.8, 48),
              256: np.linspace(e64 - 0.05, e64 + 0.9, 48), 512: np.linspace(e64 - 0.05, e64 + 0.9, 48)}
@@ -579,18 +584,17 @@ def run_serving(args, world, rank, local):
     t0 = time.perf_counter()
     for nb in cat:
         srv.add_basis(nb, *cat[nb])
-    # warm the contact caches (one short request per basis over its whole grid)
     warm = [srv.submit(nb, np.zeros(4), grids[nb], pw.FP64) for nb in cat]
     for t in warm:
         srv.wait(t)
     t_setup = time.perf_counter() - t0
-    rng = np.random.default_rng(7)
-    n_req = args.requests
+    rng = np.random.default_rng(seed)
+    logb = np.log2(np.array(sorted(cat)))
 
     def make():
         out = []
         for _ in range(n_req):
-            nb = int(2 ** rng.integers(6, 10))                    # block 64..512, log-uniform
+            nb = int(2 ** rng.integers(int(logb[0]), int(logb[-1]) + 1))   # block size, log-uniform
             N = int(rng.integers(50, 201))
             nE = int(np.exp(rng.uniform(np.log(4), np.log(32))))   # 4..32 energies, log-uniform
             E = np.sort(rng.choice(grids[nb], nE, replace=False))
@@ -606,7 +610,7 @@ def run_serving(args, world, rank, local):
     tickets = [srv.submit(*r) for r in reqs]
     solves = 0
     for t, r in zip(tickets, reqs):
-        res, _ = srv.wait(t)
+        srv.wait(t)
         solves += len(r[2])
     t_cap = time.perf_counter() - t0
     cap = solves / t_cap
@@ -634,19 +638,34 @@ def run_serving(args, world, rank, local):
     st = srv.stats()
     nbatch, nreq, largest = srv.batch_stats()
     srv.close()
-    line = {"metric": "serving: energy-solves/s and p50/p99 request latency (mixed catalog)", "value": solves / t_open,
-            "unit": "energy-solves/s", "n_gpus": 1, "higher_is_better": True, "impl": "ours",
-            "latency_s": {"p50": st["p50_s"], "p99": st["p99_s"]}, "capacity_solves_per_s": cap,
-            "arrival_rate_req_per_s": 0.7 * req_rate, "requests": n_req, "bad_status": bad, "setup_s": t_setup,
+    return {"solves_per_s": solves / t_open, "latency_s": {"p50": st["p50_s"], "p99": st["p99_s"]},
+            "capacity_solves_per_s": cap, "arrival_rate_req_per_s": 0.7 * req_rate, "requests": n_req,
+            "bad_status": bad, "setup_s": t_setup,
             "continuous_batching": {"batched_solves": nbatch, "requests": nreq, "largest_batch": largest,
                                     "rule": "queued requests of one basis with the same node count and precision "
                                             "share the next batched solve (up to 8 potentials, within the budget)"},
-            "data": "synthetic",
-            "config": {"workload": "serving", "structure": "13 nm armchair ribbon, G_cut 30 nm^-1",
-                       "catalog_block_sizes": sorted(cat), "nodes": "U[50,200]",
-                       "energies_per_request": "log-uniform 4..32 from a 48-point grid per basis",
+            "config": {"structure": "13 nm armchair ribbon, G_cut 30 nm^-1", "catalog_block_sizes": sorted(cat),
+                       "nodes": "U[50,200]", "energies_per_request": "log-uniform 4..32 from a 48-point grid per basis",
                        "precision_mix": "50% complex64 alone (PWQT_FP32), 50% mixed + refinement",
-                       "arrivals": "Poisson at 70% of the measured closed-loop request rate, seed 7"}}
+                       "arrivals": f"Poisson at 70% of the measured closed-loop request rate, seed {seed}"}}
+
+
+def run_serving(args, world, rank, local):
+    """The serving loop's own line (see serving_pass): catalog block sizes 64..512."""
+    import torch
+    from paper_1903_00548_gb300 import build as B
+
+    B.build()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    r = serving_pass(local, args.requests)
+    line = {"metric": "serving: energy-solves/s and p50/p99 request latency (mixed catalog)", "value": r["solves_per_s"],
+            "unit": "energy-solves/s", "n_gpus": 1, "higher_is_better": True, "impl": "ours",
+            "latency_s": r["latency_s"], "capacity_solves_per_s": r["capacity_solves_per_s"],
+            "arrival_rate_req_per_s": r["arrival_rate_req_per_s"], "requests": r["requests"], "bad_status": r["bad_status"],
+            "setup_s": r["setup_s"], "continuous_batching": r["continuous_batching"], "data": "synthetic",
+            "config": dict(r["config"], workload="serving")}
     print(json.dumps(line))
     return 0
 
@@ -670,7 +689,9 @@ def main(argv=None):
                     help="measure energies x bias points in one batched solve instead of the headline metric")
     ap.add_argument("--batching-workload", default="ribbon256_wide")
     ap.add_argument("--bias-points", type=int, default=8)
-    ap.add_argument("--requests", type=int, default=60, help="requests per serving pass")
+    ap.add_argument("--requests", type=int, default=60, help="requests per serving pass (--serving)")
+    ap.add_argument("--serving-requests", type=int, default=24, help="requests per pass of the default run's serving leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the default run's serving leg")
     ap.add_argument("--clocks-csv", default="/tmp/pwqt_clocks_{rank}.csv",
                     help="where the nvidia-smi clock samples of the timed region are kept ({rank} is replaced)")
     args = ap.parse_args(argv)

@@ -680,6 +680,28 @@ def error_bar(r: EnergyResult, *alts: EnergyResult) -> float:
     return bar
 
 
+def perturbation_spread(blk, U, E, eps=1e-14, samples=4, seed=0):
+    """How well FP64 input data determine T, R, T_ds at one energy: the largest change
+    when the node blocks (H0, M0 Hermitian-symmetric; H1, M1 and the extrinsic weights)
+    are perturbed by seeded random matrices of relative size eps -- the rounding that
+    any FP64 assembly of the same blocks carries -- and the system is solved again
+    with fresh contacts.  Part of the oracle's own error bar (see error_bar's callers)."""
+    rng = np.random.default_rng(seed)
+    ref = solve_energy(blk, *extrinsic_blocks(blk, U), U, E)
+    worst = 0.0
+    for _ in range(samples):
+        b = dict(blk)
+        for k in ("H0", "M0", "H1", "M1", "Wl_ll", "Wl_lr", "Wl_rr", "Wr_ll", "Wr_lr", "Wr_rr"):
+            X = blk[k]
+            P = rng.standard_normal(X.shape) + 1j * rng.standard_normal(X.shape)
+            if k in ("H0", "M0"):
+                P = 0.5 * (P + P.conj().T)
+            b[k] = X + eps * np.abs(X).max() * P
+        r = solve_energy(b, *extrinsic_blocks(b, U), U, E)
+        worst = max(worst, abs(r.T - ref.T), abs(r.T_ds - ref.T_ds), abs(r.R - ref.R))
+    return worst
+
+
 def solve_workload(sys_: System, energies, cache=None):
     cache = {} if cache is None else cache
     return [solve_energy(sys_.blk, sys_.Vd, sys_.Vu, sys_.U, float(E), cache=cache)

@@ -606,19 +606,13 @@ int compute_lead_shared(const pwqt_ctx* bz, pwqt_ctx* c, const LeadWorker& wk, d
         k_gather_cols<<<dim3((n + 127) / 128, n), b128, 0, st>>>(n, Cm.as<double2>(), didx.as<int>(), dlam.as<double2>(), BL.as<double2>());
         k_identity<<<dim3((n + 127) / 128, n), b128, 0, st>>>(n, Binv.as<double2>());
         launches += 3;
-        PWQT_TRY(lu_solve(c, wk, ls, n, B.as<double2>(), Binv.as<double2>(), n));   // B <- LU(B), Binv = B^-1
+        PWQT_TRY(lu_solve(c, wk, ls, n, B.as<double2>(), Binv.as<double2>(), n));   // Binv = B^-1
         cuDoubleComplex one = {1, 0}, zero = {0, 0}, mone = {-1, 0};
-        // T1 = B Lambda B^-1 from B's factors, not from the explicit inverse (whose error
-        // grows with cond(B) once more when multiplied out; weakly evanescent modes make B
-        // ill-conditioned): T1 B = B Lambda  <=>  B^T T1^T = (B Lambda)^T
-        transpose_c128(BL.as<double2>(), T1.as<double2>(), n, n, st);
-        PWQT_SOLVER(c, cusolverDnXgetrs(wk.sol, wk.prm, CUBLAS_OP_T, n, n, CUDA_C_64F, B.as<double2>(), n,
-                                        ls.ipiv.as<int64_t>(), CUDA_C_64F, T1.as<double2>(), n, ls.info.as<int>()));
-        transpose_c128(T1.as<double2>(), BL.as<double2>(), n, n, st);   // BL <- T1 (column-major)
-        launches += 2;
-        // Sigma = K' T1   (K'_d = K+, K'_s = K- = K+^H), column-major
+        // T1 = (B Lambda) B^-1 ; Sigma = K' T1   (K'_d = K+, K'_s = K- = K+^H), column-major
+        PWQT_BLAS(c, cublasZgemm(wk.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, BL.as<cuDoubleComplex>(), n,
+                                 Binv.as<cuDoubleComplex>(), n, &zero, T1.as<cuDoubleComplex>(), n));
         PWQT_BLAS(c, cublasZgemm(wk.blas, drain ? CUBLAS_OP_N : CUBLAS_OP_C, CUBLAS_OP_N, n, n, n, &one, Kp.as<cuDoubleComplex>(), n,
-                                 BL.as<cuDoubleComplex>(), n, &zero, S.as<cuDoubleComplex>(), n));
+                                 T1.as<cuDoubleComplex>(), n, &zero, S.as<cuDoubleComplex>(), n));
         PWQT_TRY(alloc(c, sigma, sizeof(double2) * n * n));
         transpose_c128(S.as<double2>(), sigma.as<double2>(), n, n, st);   // column-major -> row-major
         launches++;

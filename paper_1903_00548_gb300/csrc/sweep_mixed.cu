@@ -372,22 +372,32 @@ __device__ __forceinline__ void lu_offdiag(const float2* __restrict__ F, int n, 
         cp_async_commit();   // an empty group past the end keeps the wait count uniform
     };
     for (int ch = 0; ch < NSTG - 1; ++ch) fetch(ch);
+    // thread t updates column g = t % LC of rows r0 and r0 + LR / 2 of every chunk; the
+    // solved block rows kb .. kb + wd of its column stay in registers for the whole call
+    static_assert(NT / LC * 2 == LR, "two rows per thread and chunk");
+    const int g = t % LC, r0 = t / LC;
+    float2 tk[PW];
+#pragma unroll
+    for (int l = 0; l < PW; ++l) tk[l] = l < wd ? T[(kb + l) * LC + g] : make_float2(0.f, 0.f);
     for (int ch = 0; ch < nch; ++ch) {
         cp_async_wait<NSTG - 2>();
         __syncthreads();                    // chunk ch landed for every thread; chunk ch - 1 consumed
         fetch(ch + NSTG - 1);
         const float2* Fc = Fs + (size_t)(ch % NSTG) * LR * LDS;
         const int rc = r_begin + ch * LR, rows = min(LR, r_end - rc);
-        for (int q = t; q < rows * LC; q += NT) {
-            const int rr = q / LC, g = q % LC;
-            float2 a = T[(rc + rr) * LC + g];
-#pragma unroll 8
-            for (int l = 0; l < wd; ++l) {   // rows kb + l < n of T only
-                const float2 L = Fc[rr * LDS + l];
-                ffma(a, make_float2(-L.x, -L.y), T[(kb + l) * LC + g]);
-            }
-            T[(rc + rr) * LC + g] = a;
+        const bool in0 = r0 < rows, in1 = r0 + LR / 2 < rows;
+        float2 a0 = in0 ? T[(rc + r0) * LC + g] : make_float2(0.f, 0.f);
+        float2 a1 = in1 ? T[(rc + r0 + LR / 2) * LC + g] : make_float2(0.f, 0.f);
+        const float2* L0 = Fc + r0 * LDS;
+        const float2* L1 = Fc + (r0 + LR / 2) * LDS;
+#pragma unroll
+        for (int l = 0; l < PW; ++l) {      // zero-filled past wd: those terms vanish
+            const float2 x0 = L0[l], x1 = L1[l];
+            ffma(a0, make_float2(-x0.x, -x0.y), tk[l]);
+            ffma(a1, make_float2(-x1.x, -x1.y), tk[l]);
         }
+        if (in0) T[(rc + r0) * LC + g] = a0;
+        if (in1) T[(rc + r0 + LR / 2) * LC + g] = a1;
     }
     cp_async_wait<0>();
     __syncthreads();

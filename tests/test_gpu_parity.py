@@ -51,7 +51,7 @@ def _oracle_results(sys_, energies):
         r = O.solve_energy(sys_.blk, sys_.Vd, sys_.Vu, sys_.U, float(E), cache=cache)
         alts = [O.solve_energy(sys_.blk, sys_.Vd, sys_.Vu, sys_.U, float(E), cache=cache, reciprocal=k)
                 for k in (True, "cayley")]
-        r.bar = O.error_bar(r, *alts)
+        r.bar = max(O.error_bar(r, *alts), O.perturbation_spread(sys_.blk, sys_.U, float(E)))
         out.append(r)
     return out
 
@@ -60,7 +60,10 @@ def oracle_error(r):
     """The oracle's own error bar at this energy: total transmission is reciprocal
     (T_sd = T_ds exactly for a real potential), and equivalent eigen-solves (the
     reciprocal pencil, the Cayley transform) give the same modes by other rounding
-    paths, so |T - T_ds| and the spread of the three solves measure its rounding.  Where weakly evanescent modes (|lambda| ~ 0.96,
+    paths, so |T - T_ds| and the spread of the three solves measure its rounding; and
+    T is only as determined as its FP64 input blocks: the spread under perturbations of
+    the blocks at the level of assembly rounding (1e-14 relative) is part of the bar
+    (the kernels assemble the same blocks in closed form, the oracle by quadrature).  Where weakly evanescent modes (|lambda| ~ 0.96,
     from the basis near-null space) nearly coincide, the Bloch matrix B is
     ill-conditioned and this reaches ~1e-8 on the chain."""
     return r.bar

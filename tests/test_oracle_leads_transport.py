@@ -274,3 +274,18 @@ def test_degenerate_traveling_pairs():
         assert r.n_open_s == 3
         assert np.max(np.abs(r.T_modes + r.R_modes - 1.0)) < 1e-9
         assert abs(r.T - r.T_ds) < 1e-9
+
+
+def test_perturbation_spread_measures_conditioning():
+    # the oracle's conditioning estimate: tiny where T is well determined (pristine chain
+    # mid-band; the biased chain at 1.2 eV, where it grows in proportion to the
+    # perturbation once that exceeds the solve's own rounding), and ~1e-8 at the chain
+    # energy whose weakly evanescent modes make the contact ill-conditioned (there the
+    # eigen-solve's rounding dominates whatever the perturbation)
+    s0 = chain_system()
+    sp = with_potential(s0, np.zeros(20))
+    assert O.perturbation_spread(sp.blk, sp.U, 1.0) < 1e-11
+    a = O.perturbation_spread(s0.blk, s0.U, 1.2, eps=1e-14)
+    b = O.perturbation_spread(s0.blk, s0.U, 1.2, eps=1e-12)
+    assert a < 1e-12 and b > 10 * a
+    assert O.perturbation_spread(s0.blk, s0.U, 0.390625) > 1e-9

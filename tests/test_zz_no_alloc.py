@@ -63,7 +63,8 @@ def test_noalloc_matches_oracle(setup):
     for e, En in enumerate(E):
         r = O.solve_energy(s.blk, s.Vd, s.Vu, s.U, float(En), cache=cache)
         alts = [O.solve_energy(s.blk, s.Vd, s.Vu, s.U, float(En), cache=cache, reciprocal=k) for k in (True, "cayley")]
-        t = max(TOL * max(1.0, r.n_open_s), 4.0 * O.error_bar(r, *alts))
+        bar = max(O.error_bar(r, *alts), O.perturbation_spread(s.blk, s.U, float(En)))
+        t = max(TOL * max(1.0, r.n_open_s), 4.0 * bar)
         assert abs(got["T"][e] - r.T) <= t and abs(got["R"][e] - r.R) <= t, (En, got["T"][e], r.T)
 
 
