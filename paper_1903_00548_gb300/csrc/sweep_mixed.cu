@@ -14,6 +14,9 @@
 // then c_i = y_i - X_i c_{i+1} (tensor cores), FP64 copy, and refinement:
 //   r = B - A c (FP64-accurate: exact slice products on the bf16 tensor cores,
 //   residual_oz.cu), A d = r with the stored complex64 factors, c += d.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -30,13 +33,13 @@ constexpr int PW = 32;      // panel width
 constexpr int NT = 256;
 
 struct MixSys {
-    int n, N, m, w;                       // w = n + m (uniform m over the batch)
+    int n, N, m, w;                       // w = n + m rounded up to even (16-byte rows), uniform over the batch
     const double2* M0; const double2* M1; const double2* HV0; const double2* HV1;   // FP64 blocks
     const float2* M1f; const float2* HV1f;                                         // complex64 copies
     float2* F; long long sF;              // per energy N x n x n factors
     int* piv; long long sP;               // per energy N x n pivot rows
     float2* XY; long long sXY;            // per energy N x n x w
-    float2* Lb; long long sL;             // per energy n x n
+    float2* Lb; long long sL;             // per energy N x n x n couplings L_i = A_{i,i-1} (node 0 unused)
     double2* C64; double2* R64; long long sC;   // per energy N x n x m (FP64 solution, residual)
     const SweepJob* jobs;
 };
@@ -56,28 +59,20 @@ __device__ __forceinline__ float2 fdiv(float2 a, float2 b) {
 __device__ __forceinline__ float2 to32(double2 v) { return make_float2((float)v.x, (float)v.y); }
 
 // ---------------------------------------------------------------- form the node blocks
-__global__ void k_mx_form(MixSys S, int i, int only_L) {
+__global__ void k_mx_form(MixSys S, int i) {
     const int e = blockIdx.y;
     const SweepJob& J = S.jobs[e];
     const int n = S.n, N = S.N, w = S.w, ms = J.ms, md = J.md;
     const double E = J.E;
     float2* F = S.F + e * S.sF + (size_t)i * n * n;
     float2* XY = S.XY + e * S.sXY + (size_t)i * n * w;
-    float2* Lb = S.Lb + e * S.sL;
+    float2* Lb = S.Lb + e * S.sL + (size_t)i * n * n;   // kept for the correction solves
     const double2* HV0b = J.HV0 ? J.HV0 : S.HV0;
     const double2* HV1b = J.HV1 ? J.HV1 : S.HV1;
     const double2* HV0 = HV0b + (size_t)i * n * n;
     const double2* HV1 = HV1b + (size_t)i * n * n;
     const double2* HVm = HV1b + (size_t)(i > 0 ? i - 1 : 0) * n * n;
     const size_t nn = (size_t)n * n;
-    if (only_L) {
-        for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nn; t += (size_t)gridDim.x * blockDim.x) {
-            int r = (int)(t / n), c = (int)(t % n);
-            size_t tt = (size_t)c * n + r;
-            Lb[t] = to32(cconj(csub(cscale(S.M1[tt], E), HVm[tt])));
-        }
-        return;
-    }
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nn; t += (size_t)gridDim.x * blockDim.x) {
         int r = (int)(t / n), c = (int)(t % n);
         double2 d = csub(cscale(S.M0[t], E), HV0[t]);
@@ -90,9 +85,10 @@ __global__ void k_mx_form(MixSys S, int i, int only_L) {
         }
         XY[(size_t)r * w + c] = i < N - 1 ? to32(csub(cscale(S.M1[t], E), HV1[t])) : make_float2(0.f, 0.f);
     }
-    const size_t nm = (size_t)n * S.m;
+    const int wy = w - n;   // y columns: m and, for even rows, a zero padding column
+    const size_t nm = (size_t)n * wy;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nm; t += (size_t)gridDim.x * blockDim.x) {
-        int r = (int)(t / S.m), g = (int)(t % S.m);
+        int r = (int)(t / wy), g = (int)(t % wy);
         float2 v = make_float2(0.f, 0.f);
         if (i == 0 && g < ms) v = to32(J.rhs_s[(size_t)r * ms + g]);
         if (i == N - 1 && g >= ms && g < ms + md) v = to32(J.rhs_d[(size_t)r * md + (g - ms)]);
@@ -300,203 +296,341 @@ __global__ void k_mx_to64(MixSys S) {
 }
 
 // ---------------------------------------------------------------- correction solve
-// d = A^{-1} r with the stored complex64 factors; the y columns of XY_i hold the work
-// vectors.  Per node (all energies at once):  w_i = r_i - L_i w_{i-1}  (tensor cores),
-// w_i <- U_i^{-1} L_i^{-1} P_i w_i (k_mx_lusolve); then d_i = w_i - X_i d_{i+1}
-// (tensor cores) from the last node back, and c += d in FP64.
+// d = A^{-1} r with the stored complex64 factors, one launch per refinement step.  The
+// right-hand sides stay independent through the whole block-tridiagonal solve, so one
+// CTA carries LC columns of one energy through every node on its own:
+//   forward   w_i = U_i^{-1} L_i^{-1} P_i (r_i - L_i w_{i-1}),   i = 0 .. N-1
+//   backward  d_{N-1} = w_{N-1},  d_i = w_i - X_i d_{i+1},  c_i += d_i (FP64)
+// with L_i the stored coupling A_{i,i-1}, F_i = P_i^T L_i U_i the node's LU factors
+// and X_i the y-free columns of XY_i.  The CTA's two n x LC work vectors live in shared
+// memory; the matrices stream through it in 32 x 32 tiles (cp.async ring NSTG deep,
+// two 16-byte pieces per thread and tile); a tile updates 32 rows x LC columns with
+// the multiplicand's values in registers.
+// LC is picked per refinement step from the columns still refining: 16 while most
+// energies refine (fewest tile reads per column), down to 2 for the last few, where
+// the length of one CTA's chain through the nodes is the step's time.
+// The 32 x 32 diagonal blocks of the triangular factors are solved one column per
+// warp (lane = row, the solved value broadcast by shuffle).
+constexpr int TS = 32;     // tile edge
+constexpr int CT = 256;    // threads of a correction CTA
+constexpr int TILE_BYTES = TS * TS * 8;   // two 128-byte-swizzled halves of 32 rows x 16 complex64
+constexpr unsigned long long CORR_WAIT_NS = 2000000000ull;   // bounded mbarrier waits: 2 s
 
-// w_i = (complex64) r_i   (active energies)
-__global__ void k_mx_load_r(MixSys S, int i, const int* __restrict__ active) {
-    const int e = blockIdx.y;
-    if (!active[e]) return;
-    const int n = S.n, w = S.w, m = S.m;
-    float2* XY = S.XY + e * S.sXY + (size_t)i * n * w;
-    const double2* R = S.R64 + e * S.sC + (size_t)i * n * m;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)n * m; t += (size_t)gridDim.x * blockDim.x) {
-        int r = (int)(t / m), g = (int)(t % m);
-        XY[(size_t)r * w + n + g] = to32(R[t]);
-    }
+__device__ int g_corr_error = 0;
+
+// A CTA of LC columns updates TPS = 16 / LC tiles per step, one per group of 32 LC / 2
+// threads (a thread: one tile row, two columns); the ring holds NSTG tiles, two steps' worth
+// at least, so that the next step's tiles are in flight while one step computes.
+__host__ __device__ constexpr int corr_tps(int lc) { return 16 / lc; }
+__host__ __device__ constexpr int corr_nstg(int lc) { return 2 * corr_tps(lc) > 8 ? 2 * corr_tps(lc) : 8; }
+
+// shared memory: the tile ring (1024-byte aligned for the swizzle, hence the slack), its
+// mbarriers, the permutation, the two work vectors
+size_t correct_smem(int n, int lc) {
+    const size_t np = (size_t)((n + TS - 1) / TS) * TS;
+    const int nstg = corr_nstg(lc);
+    return 1024 + (size_t)nstg * TILE_BYTES + 16 * ((nstg * 8 + 15) / 16) + ((n * sizeof(int) + 15) / 16) * 16 +
+           sizeof(float2) * 2 * np * lc;
 }
 
-// w <- U^{-1} L^{-1} P w for node i.  The m right-hand sides are independent, so
-// every energy gets ceil(m / LC) CTAs of LC columns each; a CTA keeps its columns
-// in shared memory (n x LC), solves each 32-row diagonal block with one warp per
-// LC / 8 columns (lane = row, the solved value broadcast by shuffle) and applies the
-// off-diagonal part of the factors to the rows below (forward) or above
-// (backward) in parallel over (row, column).  The solve is latency-bound (a chain
-// of 2 n / 32 block steps per CTA), so LC is small: at n = 512 a CTA holds ~59 KB
-// of shared memory, three fit on an SM, and a node's launch is one wave of
-// ceil(m / 8) CTAs per energy.
-constexpr int LC = 8;
-constexpr int LCW = LC / (NT / 32);   // columns per warp in the diagonal-block solves
-static_assert(LC % (NT / 32) == 0, "every warp takes the same number of columns");
+// element (r, c) of a ring tile: half c / 16 holds 32 rows of 128 bytes whose 16-byte
+// chunks are permuted by the 128-byte swizzle (chunk ^ (r % 8))
+__device__ __forceinline__ int tile_off(int r, int c) {
+    return (c >> 4) * (TILE_BYTES / 2) + r * 128 + ((((c & 15) >> 1) ^ (r & 7)) << 4) + ((c & 1) << 3);
+}
+__device__ __forceinline__ float2 tile_at(const unsigned char* tile, int r, int c) {
+    return *reinterpret_cast<const float2*>(tile + tile_off(r, c));
+}
 
 __device__ __forceinline__ float2 shfl2(float2 v, int src) {
     return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
-
-constexpr int LR = 64;    // factor rows staged per chunk of the off-diagonal updates
-constexpr int LDS = 34;   // padded row of a staged chunk (272 B: 16-byte aligned rows, conflict-free reads)
-constexpr int NSTG = 4;   // chunks in flight per CTA
-
-size_t lusolve_smem(int n) {
-    return ((n * sizeof(int) + 15) / 16) * 16 + sizeof(float2) * (PW * (PW + 1) + (size_t)NSTG * LR * LDS + (size_t)n * LC);
+__device__ __forceinline__ uint32_t su32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ unsigned long long gclock() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait on an mbarrier phase; false when it gave up
+__device__ __forceinline__ bool corr_wait(uint32_t mbar, uint32_t parity) {
+    const unsigned long long t0 = gclock();
+    for (uint32_t it = 0;; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+        if ((it & 63) == 63 && gclock() - t0 > CORR_WAIT_NS) return false;
+    }
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int bytes) {
-    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(d), "l"(gmem), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+enum CorrPhase { PH_SCHUR, PH_LOWER, PH_UPPER };
 
-// T[r][:] -= F[r][kb .. kb+wd) T[kb .. kb+wd)[:] for rows r in [r_begin, r_end).  One CTA per
-// (energy, column group) streams about n^2 / 2 factor elements per triangle through L2, so
-// the chunks (LR rows x 32 columns, one 16-byte cp.async per two elements, rows and
-// columns past the factor zero-filled) are fetched NSTG - 1 ahead into a shared-memory ring.
-__device__ __forceinline__ void lu_offdiag(const float2* __restrict__ F, int n, int kb, int wd, int r_begin, int r_end,
-                                           float2* Fs, float2* T) {
-    const int t = threadIdx.x;
-    const int nch = (r_end - r_begin + LR - 1) / LR;
-    auto fetch = [&](int ch) {
-        if (ch < nch) {
-            float2* dst = Fs + (size_t)(ch % NSTG) * LR * LDS;
-            const int rc = r_begin + ch * LR;
-            for (int q = t; q < LR * (PW / 2); q += NT) {     // 16-byte pieces: row rr, columns 2l, 2l + 1
-                const int rr = q / (PW / 2), l2 = 2 * (q % (PW / 2));
-                const bool in = rc + rr < r_end && l2 < wd;
-                const float2* src = in ? F + (size_t)(rc + rr) * n + kb + l2 : F;
-                cp_async16(dst + rr * LDS + l2, src, in ? (l2 + 1 < wd ? 16 : 8) : 0);
+// Steps of a phase, in tile order: SCHUR (and the backward X_i product) per column panel
+// kb the row blocks 0 .. nbk-1, TPS at a time; LOWER per panel kb the diagonal block (a
+// step of its own), then the blocks below it; UPPER from the last panel, the diagonal
+// block, then the blocks above it.  The tiles of one step update distinct row blocks.
+struct StepCursor {
+    int kb, rb0, cnt;    // cnt == 0: the diagonal block of panel kb
+    __device__ void first(int ph, int nbk, int tps) {
+        if (ph == PH_SCHUR) { kb = 0; rb0 = 0; cnt = min(tps, nbk); }
+        else { kb = ph == PH_LOWER ? 0 : nbk - 1; rb0 = kb; cnt = 0; }
+    }
+    // advance; false past the phase's last step
+    __device__ bool next(int ph, int nbk, int tps) {
+        if (ph == PH_SCHUR) {
+            rb0 += cnt;
+            if (rb0 == nbk) { if (++kb == nbk) return false; rb0 = 0; }
+            cnt = min(tps, nbk - rb0);
+        } else if (ph == PH_LOWER) {
+            rb0 = cnt == 0 ? kb + 1 : rb0 + cnt;
+            if (rb0 == nbk) { if (++kb == nbk) return false; rb0 = kb; cnt = 0; }
+            else cnt = min(tps, nbk - rb0);
+        } else {
+            rb0 = cnt == 0 ? 0 : rb0 + cnt;
+            if (rb0 == kb) { if (--kb < 0) return false; rb0 = kb; cnt = 0; }
+            else cnt = min(tps, kb - rb0);
+        }
+        return true;
+    }
+    __device__ int tiles() const { return cnt == 0 ? 1 : cnt; }
+};
+
+// The ring of a CTA: tile j (counted over the whole kernel) sits in slot j % NSTG and
+// completes phase (j / NSTG) & 1 of that slot's mbarrier.
+struct CorrRing {
+    unsigned char* buf;
+    uint32_t mbar;       // shared address of NSTG consecutive mbarriers
+    int* abort;          // shared flag: a wait gave up
+};
+
+// One phase over the matrices of tensor map tm (matrix index mat, n x n used): SCHUR
+// T -= M V (T and V distinct n x LC vectors), LOWER/UPPER  V <- M^{-1} V with the unit
+// lower / upper triangle of the LU factors.  A step updates TPS row blocks at once, one
+// tile per group of TG = 256 / TPS threads; a thread of a group takes row rr of its tile
+// and columns gq, gq + GW (GW = LC / 2), the multiplicand's 32 rows of those columns in
+// registers (reloaded when the column panel changes), so that a tile row costs 16
+// shared-memory loads and 256 FMAs whatever LC is.  A diagonal block is a step of its
+// own: warp w solves columns w, w + 8 < LC (lane = row, the solved value broadcast by
+// shuffle).  Thread 0 fetches: two tensor-map copies per tile (the 16-column halves,
+// 128-byte swizzle) completing on the slot's mbarrier; the map's bounds (n columns, n rows
+// per matrix) zero-fill the edge tiles.  Tiles base .. of the kernel's count; returns the
+// next base, or -1 when a wait gave up (after the copies in flight have landed or timed out).
+template <int LC>
+__device__ __noinline__ int corr_phase(int ph, const CUtensorMap* tm, int mat, int n, CorrRing R, int base, float2* V, float2* T) {
+    constexpr int TPS = corr_tps(LC), NSTG = corr_nstg(LC);
+    constexpr int GW = LC / 2, TG = CT / TPS;
+    static_assert(TG == TS * GW, "a group: 32 rows x GW column pairs");
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int tw = t / TG, gq = t % GW, rr = (t % TG) / GW;
+    const int nbk = (n + TS - 1) / TS;
+    const int ntiles = ph == PH_SCHUR ? nbk * nbk : nbk * (nbk + 1) / 2;
+    StepCursor fc, cc;      // fetch cursor (tile granularity through fsub), compute cursor
+    fc.first(ph, nbk, TPS);
+    cc.first(ph, nbk, TPS);
+    int fsub = 0, issued = 0;
+    // issue the tiles up to (not including) tile `upto` of the phase
+    auto fetch_to = [&](int upto) {
+        upto = min(upto, ntiles);
+        while (issued < upto) {
+            if (t == 0) {
+                const uint32_t j = (uint32_t)(base + issued), slot = j % NSTG;
+                const uint32_t dst = su32(R.buf + (size_t)slot * TILE_BYTES), mb = R.mbar + 8 * slot;
+                const int rb = fc.cnt == 0 ? fc.kb : fc.rb0 + fsub;
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mb), "r"((uint32_t)TILE_BYTES) : "memory");
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    asm volatile(
+                        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                        :: "r"(dst + h * (TILE_BYTES / 2)), "l"(reinterpret_cast<uint64_t>(tm)), "r"(fc.kb * TS + 16 * h),
+                           "r"(rb * TS), "r"(mat), "r"(mb)
+                        : "memory");
+            }
+            ++issued;
+            if (++fsub == fc.tiles()) { fsub = 0; fc.next(ph, nbk, TPS); }
+        }
+    };
+    fetch_to(NSTG);
+    float2 tk[2][TS];
+    float2* Tgt = ph == PH_SCHUR ? T : V;
+    int done = 0;
+    for (bool more = true; more; more = cc.next(ph, nbk, TPS)) {
+        const int nt = cc.tiles();
+        // this thread's tile of the step (the diagonal block: every thread's)
+        const int mine = cc.cnt == 0 ? 0 : min(tw, nt - 1);
+        const uint32_t j = (uint32_t)(base + done + mine), slot = j % NSTG;
+        if (!corr_wait(R.mbar + 8 * slot, (j / NSTG) & 1)) {
+            *R.abort = 1;
+            atomicExch(&g_corr_error, 1);
+        }
+        __syncthreads();          // the step's tiles landed; the previous step's consumed; V, T settled
+        if (*R.abort) {
+            // wait (bounded again) for the copies still in flight before the CTA stops
+            if (t == 0)
+                for (int q = done; q < issued; ++q) corr_wait(R.mbar + 8 * ((base + q) % NSTG), ((base + q) / NSTG) & 1);
+            return -1;
+        }
+        fetch_to(done + NSTG);    // refill the slots of the steps consumed so far
+        const int kb = cc.kb;
+        if (cc.cnt == 0) {
+            // diagonal block: columns warp, warp + 8 of V rows kb*32 .. +32 (rows past n are
+            // zero and their zero-filled tile rows keep them so)
+            const unsigned char* tile = R.buf + (size_t)((base + done) % NSTG) * TILE_BYTES;
+            constexpr int DC = (LC + CT / 32 - 1) / (CT / 32);   // columns per warp, solved side by side
+            if (warp < LC) {
+                float2 v[DC];
+#pragma unroll
+                for (int d = 0; d < DC; ++d) v[d] = V[(kb * TS + lane) * LC + warp + d * (CT / 32)];
+                if (ph == PH_LOWER) {
+                    for (int jj = 0; jj + 1 < TS; ++jj) {
+                        const float2 Lv = tile_at(tile, lane, jj);
+#pragma unroll
+                        for (int d = 0; d < DC; ++d) {
+                            const float2 aj = shfl2(v[d], jj);
+                            if (lane > jj) ffma(v[d], make_float2(-Lv.x, -Lv.y), aj);
+                        }
+                    }
+                } else {
+                    for (int jj = TS - 1; jj >= 0; --jj) {
+                        float2 dg = tile_at(tile, jj, jj);
+                        if (dg.x == 0.f && dg.y == 0.f) dg = make_float2(1.f, 0.f);   // flagged by the factorisation
+                        const float2 Uv = tile_at(tile, lane, jj);
+#pragma unroll
+                        for (int d = 0; d < DC; ++d) {
+                            if (lane == jj) v[d] = fdiv(v[d], dg);
+                            const float2 aj = shfl2(v[d], jj);
+                            if (lane < jj) ffma(v[d], make_float2(-Uv.x, -Uv.y), aj);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int d = 0; d < DC; ++d) V[(kb * TS + lane) * LC + warp + d * (CT / 32)] = v[d];
+            }
+        } else {
+            const bool first = ph == PH_LOWER ? cc.rb0 == kb + 1 : cc.rb0 == 0;
+            if (first) {
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+#pragma unroll
+                    for (int l = 0; l < TS; ++l) tk[k][l] = V[(kb * TS + l) * LC + gq + k * GW];
+            }
+            if (tw < nt) {
+                const unsigned char* trow = R.buf + (size_t)((base + done + tw) % NSTG) * TILE_BYTES + rr * 128;
+                const int sw = rr & 7;
+                float2 a0[2], a1[2];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) a0[k] = a1[k] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int c2 = 0; c2 < TS / 2; ++c2) {   // 16-byte chunk c2 of the row: columns 2 c2, 2 c2 + 1
+                    const float4 x = *reinterpret_cast<const float4*>(trow + (c2 >> 3) * (TILE_BYTES / 2) + (((c2 & 7) ^ sw) << 4));
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        ffma(a0[k], make_float2(-x.x, -x.y), tk[k][2 * c2]);
+                        ffma(a1[k], make_float2(-x.z, -x.w), tk[k][2 * c2 + 1]);
+                    }
+                }
+                float2* out = Tgt + ((cc.rb0 + tw) * TS + rr) * LC + gq;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const float2 o0 = out[k * GW];
+                    out[k * GW] = make_float2(o0.x + a0[k].x + a1[k].x, o0.y + a0[k].y + a1[k].y);
+                }
             }
         }
-        cp_async_commit();   // an empty group past the end keeps the wait count uniform
-    };
-    for (int ch = 0; ch < NSTG - 1; ++ch) fetch(ch);
-    // thread t updates column g = t % LC of rows r0 and r0 + LR / 2 of every chunk; the
-    // solved block rows kb .. kb + wd of its column stay in registers for the whole call
-    static_assert(NT / LC * 2 == LR, "two rows per thread and chunk");
-    const int g = t % LC, r0 = t / LC;
-    float2 tk[PW];
-#pragma unroll
-    for (int l = 0; l < PW; ++l) tk[l] = l < wd ? T[(kb + l) * LC + g] : make_float2(0.f, 0.f);
-    for (int ch = 0; ch < nch; ++ch) {
-        cp_async_wait<NSTG - 2>();
-        __syncthreads();                    // chunk ch landed for every thread; chunk ch - 1 consumed
-        fetch(ch + NSTG - 1);
-        const float2* Fc = Fs + (size_t)(ch % NSTG) * LR * LDS;
-        const int rc = r_begin + ch * LR, rows = min(LR, r_end - rc);
-        const bool in0 = r0 < rows, in1 = r0 + LR / 2 < rows;
-        float2 a0 = in0 ? T[(rc + r0) * LC + g] : make_float2(0.f, 0.f);
-        float2 a1 = in1 ? T[(rc + r0 + LR / 2) * LC + g] : make_float2(0.f, 0.f);
-        const float2* L0 = Fc + r0 * LDS;
-        const float2* L1 = Fc + (r0 + LR / 2) * LDS;
-#pragma unroll
-        for (int l = 0; l < PW; ++l) {      // zero-filled past wd: those terms vanish
-            const float2 x0 = L0[l], x1 = L1[l];
-            ffma(a0, make_float2(-x0.x, -x0.y), tk[l]);
-            ffma(a1, make_float2(-x1.x, -x1.y), tk[l]);
-        }
-        if (in0) T[(rc + r0) * LC + g] = a0;
-        if (in1) T[(rc + r0 + LR / 2) * LC + g] = a1;
+        done += nt;
     }
-    cp_async_wait<0>();
     __syncthreads();
+    return base + ntiles;
 }
 
-__global__ void __launch_bounds__(NT) k_mx_lusolve(MixSys S, int i, const int* __restrict__ active) {
+template <int LC>
+__global__ void __launch_bounds__(CT) k_mx_correct(MixSys S, const int* __restrict__ active, const __grid_constant__ CUtensorMap tmL,
+                                                   const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmX) {
+    constexpr int NT = CT, NSTG = corr_nstg(LC);
     const int e = blockIdx.x;
     if (!active[e]) return;
     const SweepJob& J = S.jobs[e];
-    const int n = S.n, w = S.w, m = J.ms + J.md;
+    const int n = S.n, N = S.N, w = S.w, m = S.m;
     const int c0 = blockIdx.y * LC;
-    if (c0 >= m) return;
-    extern __shared__ unsigned char sm[];
-    int* perm = reinterpret_cast<int*>(sm);                                              // n
-    float2* Ld = reinterpret_cast<float2*>(sm + ((n * sizeof(int) + 15) / 16) * 16);     // PW x (PW+1)
-    float2* Fs = Ld + PW * (PW + 1);                                                     // NSTG x LR x LDS
-    float2* T = Fs + NSTG * LR * LDS;                                                    // n x LC
-    const float2* F = S.F + e * S.sF + (size_t)i * n * n;
-    const int* pg = S.piv + e * S.sP + (size_t)i * n;        // row permutation (k_mx_perm)
-    float2* W = S.XY + e * S.sXY + (size_t)i * n * w + n;     // row stride w
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    for (int j = t; j < n; j += NT) perm[j] = pg[j];
+    const int ncol = min(LC, J.ms + J.md - c0);
+    if (ncol <= 0) return;
+    const int np = ((n + TS - 1) / TS) * TS;
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ int abort_flag;
+    unsigned char* ring = sm + ((1024 - (su32(sm) & 1023)) & 1023);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(ring + (size_t)NSTG * TILE_BYTES);
+    int* perm = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(mbar) + 16 * ((NSTG * 8 + 15) / 16));
+    float2* Wv = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(perm) + ((n * sizeof(int) + 15) / 16) * 16);   // w_i / d_{i+1}
+    float2* Sv = Wv + (size_t)np * LC;       // scratch: r_i - L_i w_{i-1} (forward), d_i (backward)
+    const int t = threadIdx.x;
+    if (t == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < NSTG; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(mbar + s)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int q = t; q < 2 * np * LC; q += NT) Wv[q] = make_float2(0.f, 0.f);   // rows past n stay zero
     __syncthreads();
-#pragma unroll 8
-    for (int q = t; q < n * LC; q += NT) {
-        const int r = q / LC, g = q % LC;
-        T[q] = c0 + g < m ? W[(size_t)perm[r] * w + c0 + g] : make_float2(0.f, 0.f);
+    const CorrRing R{ring, su32(mbar), &abort_flag};
+    int base = 0;
+    const int mat0 = e * N;   // tensor-map matrix index of (energy e, node 0)
+    float2* XYe = S.XY + e * S.sXY;
+    const int* pe = S.piv + e * S.sP;
+    const double2* Re = S.R64 + e * S.sC;
+    double2* Ce = S.C64 + e * S.sC;
+    const size_t nw = (size_t)n * w, nm = (size_t)n * m;
+    for (int i = 0; i < N && base >= 0; ++i) {
+        for (int j = t; j < n; j += NT) perm[j] = pe[(size_t)i * n + j];
+        __syncthreads();
+        const double2* Ri = Re + i * nm;
+        if (i == 0) {
+            for (int q = t; q < n * LC; q += NT) {
+                const int r = q / LC, g = q % LC;
+                Wv[q] = g < ncol ? to32(Ri[(size_t)perm[r] * m + c0 + g]) : make_float2(0.f, 0.f);
+            }
+        } else {
+            for (int q = t; q < n * LC; q += NT) {
+                const int r = q / LC, g = q % LC;
+                Sv[q] = g < ncol ? to32(Ri[(size_t)r * m + c0 + g]) : make_float2(0.f, 0.f);
+            }
+            base = corr_phase<LC>(PH_SCHUR, &tmL, mat0 + i, n, R, base, Wv, Sv);   // Sv -= L_i w_{i-1}
+            if (base < 0) break;
+            for (int q = t; q < n * LC; q += NT) Wv[q] = Sv[perm[q / LC] * LC + q % LC];
+        }
+        base = corr_phase<LC>(PH_LOWER, &tmF, mat0 + i, n, R, base, Wv, Sv);
+        if (base < 0) break;
+        base = corr_phase<LC>(PH_UPPER, &tmF, mat0 + i, n, R, base, Wv, Sv);
+        if (base < 0) break;
+        float2* Yi = XYe + i * nw + n + c0;
+        for (int q = t; q < n * LC; q += NT) {
+            const int r = q / LC, g = q % LC;
+            if (g < ncol) Yi[(size_t)r * w + g] = Wv[q];
+        }
     }
-    __syncthreads();
-    // forward substitution, unit lower factor
-    for (int kb = 0; kb < n; kb += PW) {
-        const int wd = min(PW, n - kb);
-        {
-            float2 v[PW * PW / NT];
-#pragma unroll
-            for (int u = 0; u < PW * PW / NT; ++u) {
-                const int q = t + u * NT, r = q / PW, c = q % PW;
-                v[u] = (r < wd && c < wd) ? F[(size_t)(kb + r) * n + kb + c] : make_float2(0.f, 0.f);
+    // backward; each thread reads back only the (row, column) entries it wrote
+    for (int i = N - 1; i >= 0 && base >= 0; --i) {
+        if (i < N - 1) {
+            const float2* Yi = XYe + i * nw + n + c0;
+            for (int q = t; q < n * LC; q += NT) {
+                const int r = q / LC, g = q % LC;
+                Sv[q] = g < ncol ? Yi[(size_t)r * w + g] : make_float2(0.f, 0.f);
             }
-#pragma unroll
-            for (int u = 0; u < PW * PW / NT; ++u) {
-                const int q = t + u * NT;
-                Ld[(q / PW) * (PW + 1) + q % PW] = v[u];
+            base = corr_phase<LC>(PH_SCHUR, &tmX, mat0 + i, n, R, base, Wv, Sv);   // Sv -= X_i d_{i+1}
+            if (base < 0) break;
+            float2* x = Wv; Wv = Sv; Sv = x;
+        }
+        double2* Ci = Ce + i * nm + c0;
+        for (int q = t; q < n * LC; q += NT) {
+            const int r = q / LC, g = q % LC;
+            if (g < ncol) {
+                const float2 d = Wv[q];
+                double2& c = Ci[(size_t)r * m + g];
+                c.x += d.x;
+                c.y += d.y;
             }
         }
-        __syncthreads();
-        for (int cc = LCW * warp; cc < LCW * (warp + 1); ++cc) {
-            float2 v = lane < wd ? T[(kb + lane) * LC + cc] : make_float2(0.f, 0.f);
-            for (int j = 0; j + 1 < wd; ++j) {
-                const float2 aj = shfl2(v, j);
-                if (lane > j) {
-                    const float2 L = Ld[lane * (PW + 1) + j];
-                    ffma(v, make_float2(-L.x, -L.y), aj);
-                }
-            }
-            if (lane < wd) T[(kb + lane) * LC + cc] = v;
-        }
-        __syncthreads();
-        lu_offdiag(F, n, kb, wd, kb + wd, n, Fs, T);
-    }
-    // backward substitution, upper factor with its diagonal
-    for (int kb = ((n - 1) / PW) * PW; kb >= 0; kb -= PW) {
-        const int wd = min(PW, n - kb);
-        {
-            float2 v[PW * PW / NT];
-#pragma unroll
-            for (int u = 0; u < PW * PW / NT; ++u) {
-                const int q = t + u * NT, r = q / PW, c = q % PW;
-                v[u] = (r < wd && c < wd) ? F[(size_t)(kb + r) * n + kb + c] : make_float2(r == c ? 1.f : 0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < PW * PW / NT; ++u) {
-                const int q = t + u * NT;
-                Ld[(q / PW) * (PW + 1) + q % PW] = v[u];
-            }
-        }
-        __syncthreads();
-        for (int cc = LCW * warp; cc < LCW * (warp + 1); ++cc) {
-            float2 v = lane < wd ? T[(kb + lane) * LC + cc] : make_float2(0.f, 0.f);
-            for (int j = wd - 1; j >= 0; --j) {
-                if (lane == j) {
-                    float2 d = Ld[j * (PW + 1) + j];
-                    if (d.x == 0.f && d.y == 0.f) d = make_float2(1.f, 0.f);
-                    v = fdiv(v, d);
-                }
-                const float2 aj = shfl2(v, j);
-                if (lane < j) {
-                    const float2 U = Ld[lane * (PW + 1) + j];
-                    ffma(v, make_float2(-U.x, -U.y), aj);
-                }
-            }
-            if (lane < wd) T[(kb + lane) * LC + cc] = v;
-        }
-        __syncthreads();
-        lu_offdiag(F, n, kb, wd, 0, kb, Fs, T);
-    }
-    for (int q = t; q < n * LC; q += NT) {
-        const int r = q / LC, g = q % LC;
-        if (c0 + g < m) W[(size_t)r * w + c0 + g] = T[q];
     }
 }
 
@@ -521,22 +655,6 @@ __global__ void k_mx_perm(MixSys S) {
     for (int j = threadIdx.x; j < n; j += blockDim.x) piv[j] = perm[j];
 }
 
-// c += d (FP64), active energies
-__global__ void k_mx_update(MixSys S, const int* __restrict__ active) {
-    const int e = blockIdx.y;
-    if (!active[e]) return;
-    const int n = S.n, N = S.N, m = S.m, w = S.w;
-    const size_t tot = (size_t)N * n * m;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
-        size_t i = t / ((size_t)n * m), rem = t % ((size_t)n * m);
-        int r = (int)(rem / m), g = (int)(rem % m);
-        float2 d = S.XY[e * S.sXY + i * n * w + (size_t)r * w + n + g];
-        double2& c = S.C64[e * S.sC + t];
-        c.x += d.x;
-        c.y += d.y;
-    }
-}
-
 __global__ void k_or_status(const SweepJob* __restrict__ jobs, const int* __restrict__ bits, int nb) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < nb && bits[b]) atomicOr(jobs[b].status, bits[b]);
@@ -544,9 +662,46 @@ __global__ void k_or_status(const SweepJob* __restrict__ jobs, const int* __rest
 
 }  // namespace
 
+namespace {
+// 3D tensor map (columns, rows, matrix) over `count` consecutive n x n complex64 matrices of
+// row stride ld (elements), boxes of 16 columns x 32 rows, 128-byte swizzle, zero fill
+// past the bounds
+bool corr_tensor_map(CUtensorMap* tm, const float2* base, int n, int ld, long long count) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q{};
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)count};
+    const cuuint64_t strides[2] = {(cuuint64_t)ld * 8, (cuuint64_t)n * ld * 8};
+    const cuuint32_t box[3] = {16, (cuuint32_t)TS, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<float2*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int corr_error_flag(bool reset, cudaStream_t st) {
+    int v = 0;
+    cudaMemcpyFromSymbolAsync(&v, g_corr_error, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    if (reset && v) {
+        const int zero = 0;
+        cudaMemcpyToSymbolAsync(g_corr_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+        cudaStreamSynchronize(st);
+    }
+    return v;
+}
+}  // namespace
+
 size_t mixed_bytes_per_energy(int n, int N, int m) {
-    // F + XY (complex64) + pivots + L scratch + FP64 solution and residual
-    return sizeof(float2) * ((size_t)N * n * n + (size_t)N * n * (n + m) + (size_t)n * std::max(n, m)) + sizeof(int) * (size_t)N * n +
+    // F + XY + L_i (complex64) + pivots + FP64 solution and residual
+    const size_t w = (size_t)n + m + (m & 1);
+    return sizeof(float2) * ((size_t)N * n * n + (size_t)N * n * w + (size_t)N * n * n) + sizeof(int) * (size_t)N * n +
            3 * sizeof(double2) * (size_t)N * n * m +     // FP64 solution, residual, float-float copy
            2 * oz::panel_item_bytes(n, 1) +               // self-energy slice panels
            oz::b_bytes(n, N, m + 32);                     // solution slices (a column tile of slack)
@@ -591,10 +746,12 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
     // idempotent (a function attribute of the device): set per call, no flag shared between host threads
     if (cgemm_tc_init() != 0) return fail(c, PWQT_ERR_CUDA, "tensor-core GEMM set-up failed");
     const int n = sys.n, N = sys.N;
+    // the complex64 rows of the factors start on 16-byte boundaries (bulk and cp.async copies)
+    if (n % 2) return fail(c, PWQT_ERR_INVALID_ARG, "mixed precision needs an even block size (use PWQT_FP64)");
     int m = 0;
     for (int b = 0; b < nb; ++b) m = std::max(m, jobs[b].ms + jobs[b].md);
     m = std::max(m, 1);
-    const int w = n + m;
+    const int w = n + m + (m & 1);   // even: the rows of XY_i start on 16-byte boundaries (tile copies)
     MixSys S;
     S.n = n; S.N = N; S.m = m; S.w = w;
     S.M0 = sys.M0; S.M1 = sys.M1; S.HV0 = sys.HV0; S.HV1 = sys.HV1;
@@ -602,7 +759,7 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
     S.sF = (long long)N * n * n;
     S.sP = (long long)N * n;
     S.sXY = (long long)N * n * w;
-    S.sL = (long long)n * std::max(n, m);   // L_i (n x n), reused as the n x m correction scratch
+    S.sL = (long long)N * n * n;
     S.sC = (long long)N * n * m;
     const size_t bytes = mixed_bytes_per_energy(n, N, m) * nb + 1024 * 4;
     PWQT_TRY(ensure(c, L.ws_mixed, bytes));
@@ -634,11 +791,10 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
     // the limit is a property of the kernel, shared by every context in the process (several
     // contexts on several host threads run here at once): always the device maximum, never a
     // per-call value that another thread could lower under a launch in flight
-    cudaFuncAttributes fa_panel{}, fa_lus{};
+    cudaFuncAttributes fa_panel{};
     PWQT_CUDA(c, cudaFuncGetAttributes(&fa_panel, k_mx_panel));
-    PWQT_CUDA(c, cudaFuncGetAttributes(&fa_lus, k_mx_lusolve));
     // the opt-in maximum counts static and dynamic shared memory together
-    const int dyn_panel = smem_optin - (int)fa_panel.sharedSizeBytes, dyn_lus = smem_optin - (int)fa_lus.sharedSizeBytes;
+    const int dyn_panel = smem_optin - (int)fa_panel.sharedSizeBytes;
     if (panel_smem > (size_t)dyn_panel) return fail(c, PWQT_ERR_INVALID_ARG, "panel exceeds shared memory");
     PWQT_CUDA(c, cudaFuncSetAttribute(k_mx_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_panel));
     auto gemm = [&](const float2* A, long long sA, int lda, const float2* B1, long long sB1, int ldb1, const float2* B2, long long sB2,
@@ -651,11 +807,11 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
     for (int i = 0; i < N; ++i) {
         float2* Fi = S.F + (size_t)i * n * n;
         float2* XYi = S.XY + (size_t)i * n * w;
-        k_mx_form<<<dim3(fblocks, nb), NT, 0, st>>>(S, i, 0);
+        k_mx_form<<<dim3(fblocks, nb), NT, 0, st>>>(S, i);
         c->launches++;
         if (i > 0) {
             const float2* XYp = S.XY + (size_t)(i - 1) * n * w;
-            gemm(S.Lb, S.sL, n, XYp, S.sXY, w, XYp + n, S.sXY, w, Fi, S.sF, n, XYi + n, S.sXY, w, n, n, w, n);
+            gemm(S.Lb + (size_t)i * n * n, S.sL, n, XYp, S.sXY, w, XYp + n, S.sXY, w, Fi, S.sF, n, XYi + n, S.sXY, w, n, n, w, n);
         }
         for (int k0 = 0; k0 < n; k0 += PW) {
             const int wd = std::min(PW, n - k0);
@@ -705,9 +861,36 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         res[b].r_row_stride = m;
     }
     PWQT_CUDA(c, cudaMemcpyAsync(res_d, res.data(), sizeof(ResJob) * nb, cudaMemcpyHostToDevice, st));
-    const size_t lus_smem = lusolve_smem(n);
-    if (lus_smem > (size_t)dyn_lus) return fail(c, PWQT_ERR_INVALID_ARG, "correction solve exceeds shared memory");
-    PWQT_CUDA(c, cudaFuncSetAttribute(k_mx_lusolve, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_lus));
+    // correction solve: the column counts per CTA whose two n x LC work vectors fit
+    const void* corr_fn[4] = {(const void*)k_mx_correct<16>, (const void*)k_mx_correct<8>, (const void*)k_mx_correct<4>,
+                              (const void*)k_mx_correct<2>};
+    const int corr_lcs[4] = {16, 8, 4, 2};
+    bool corr_fits[4];
+    for (int k = 0; k < 4; ++k) {
+        cudaFuncAttributes fa{};
+        PWQT_CUDA(c, cudaFuncGetAttributes(&fa, corr_fn[k]));
+        const int dyn = smem_optin - (int)fa.sharedSizeBytes;
+        corr_fits[k] = correct_smem(n, corr_lcs[k]) <= (size_t)dyn;
+        if (corr_fits[k]) PWQT_CUDA(c, cudaFuncSetAttribute(corr_fn[k], cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+    }
+    if (!corr_fits[3]) return fail(c, PWQT_ERR_INVALID_ARG, "correction solve exceeds shared memory");
+    // tensor maps of the stored couplings L_i, factors F_i and X_i (the first n columns of XY_i)
+    CUtensorMap tmL, tmF, tmX;
+    if (!corr_tensor_map(&tmL, S.Lb, n, n, (long long)nb * N) || !corr_tensor_map(&tmF, S.F, n, n, (long long)nb * N) ||
+        !corr_tensor_map(&tmX, S.XY, n, w, (long long)nb * N))
+        return fail(c, PWQT_ERR_CUDA, "correction solve: tensor map encoding failed");
+    // the widest CTA that still gives half the SMs a CTA of this lane (the other lane
+    // takes the rest); with fewer columns left the narrowest that fits
+    auto corr_pick = [&](const std::vector<int>& act) {
+        for (int k = 0; k < 4; ++k) {
+            if (!corr_fits[k]) continue;
+            long ctas = 0;
+            for (int b = 0; b < nb; ++b)
+                if (act[b]) ctas += (jobs[b].ms + jobs[b].md + corr_lcs[k] - 1) / corr_lcs[k];
+            if (2 * ctas >= c->sm_count) return k;
+        }
+        return 3;
+    };
     std::vector<double> resid(nb, 1.0), prev(nb, 1e300);
     std::vector<int> iters(nb, 0), active(nb, 1), stall(nb, 0), bits(nb, 0);
     const double tol = c->opts.ir_tol;
@@ -859,30 +1042,19 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
             L.prof_ir_iters++;
         }
         PWQT_CUDA(c, cudaMemcpyAsync(active_d, active.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
-        for (int i = 0; i < N; ++i) {
-            float2* XYi = S.XY + (size_t)i * n * w;
-            k_mx_load_r<<<dim3(64, nb), NT, 0, st>>>(S, i, active_d);
-            c->launches++;
-            if (i > 0) {
-                k_mx_form<<<dim3(fblocks, nb), NT, 0, st>>>(S, i, 1);
-                const float2* XYp = S.XY + (size_t)(i - 1) * n * w;
-                gemm(S.Lb, S.sL, n, XYp + n, S.sXY, w, XYp + n, S.sXY, w, XYi + n, S.sXY, w, XYi + n, S.sXY, w, m, n, m, n);
-                c->launches++;
-            }
-            k_mx_lusolve<<<dim3(nb, (m + LC - 1) / LC), NT, lus_smem, st>>>(S, i, active_d);
-            c->launches++;
-        }
-        for (int i = N - 2; i >= 0; --i) {
-            float2* XYi = S.XY + (size_t)i * n * w;
-            const float2* XYn = S.XY + (size_t)(i + 1) * n * w;
-            gemm(XYi, S.sXY, w, XYn + n, S.sXY, w, XYn + n, S.sXY, w, XYi + n, S.sXY, w, XYi + n, S.sXY, w, m, n, m, n);
-        }
-        k_mx_update<<<dim3(256, nb), NT, 0, st>>>(S, active_d);
+        const int ck = corr_pick(active), lc = corr_lcs[ck];
+        const dim3 cgrid(nb, (m + lc - 1) / lc);
+        const size_t csm = correct_smem(n, lc);
+        if (lc == 16) k_mx_correct<16><<<cgrid, CT, csm, st>>>(S, active_d, tmL, tmF, tmX);
+        else if (lc == 8) k_mx_correct<8><<<cgrid, CT, csm, st>>>(S, active_d, tmL, tmF, tmX);
+        else if (lc == 4) k_mx_correct<4><<<cgrid, CT, csm, st>>>(S, active_d, tmL, tmF, tmX);
+        else k_mx_correct<2><<<cgrid, CT, csm, st>>>(S, active_d, tmL, tmF, tmX);
         c->launches++;
         if (c->profile) PWQT_CUDA(c, cudaEventRecord(L.ev[3], st));
         PWQT_CUDA(c, cudaGetLastError());
     }
     if (sliced && oz::error_flag(true, st)) return fail(c, PWQT_ERR_TIMEOUT, "slice-product residual: a bounded mbarrier wait gave up");
+    if (corr_error_flag(true, st)) return fail(c, PWQT_ERR_TIMEOUT, "correction solve: a bounded mbarrier wait gave up");
     PWQT_CUDA(c, cudaMemcpyAsync(iters_dev, iters.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
     PWQT_CUDA(c, cudaMemcpyAsync(bits_d, bits.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
     k_or_status<<<(nb + 127) / 128, 128, 0, st>>>(jobs_d, bits_d, nb);
