@@ -413,8 +413,9 @@ struct CorrRing {
 // and columns gq, gq + GW (GW = LC / 2), the multiplicand's 32 rows of those columns in
 // registers (reloaded when the column panel changes), so that a tile row costs 16
 // shared-memory loads and 256 FMAs whatever LC is.  A diagonal block is a step of its
-// own: warp w solves columns w, w + 8 < LC (lane = row, the solved value broadcast by
-// shuffle).  Thread 0 fetches: two tensor-map copies per tile (the 16-column halves,
+// own: the factorisation left the inverses of the diagonal blocks of L and U in place
+// (k_mx_diag_inv), so the step is one more triangular tile product, with no dependent
+// chain.  Lane 0 of each warp fetches in turn: two tensor-map copies per tile (the 16-column halves,
 // 128-byte swizzle) completing on the slot's mbarrier; the map's bounds (n columns, n rows
 // per matrix) zero-fill the edge tiles.  Tiles base .. of the kernel's count; returns the
 // next base, or -1 when a wait gave up (after the copies in flight have landed or timed out).
@@ -434,8 +435,8 @@ __device__ __noinline__ int corr_phase(int ph, const CUtensorMap* tm, int mat, i
     // issue the tiles up to (not including) tile `upto` of the phase
     auto fetch_to = [&](int upto) {
         upto = min(upto, ntiles);
-        while (issued < upto) {
-            if (t == 0) {
+        for (int q = 0; issued < upto; ++q) {
+            if (t == 32 * (q % (CT / 32))) {   // lane 0 of warp q % 8 issues the call's q-th tile
                 const uint32_t j = (uint32_t)(base + issued), slot = j % NSTG;
                 const uint32_t dst = su32(R.buf + (size_t)slot * TILE_BYTES), mb = R.mbar + 8 * slot;
                 const int rb = fc.cnt == 0 ? fc.kb : fc.rb0 + fsub;
@@ -476,38 +477,48 @@ __device__ __noinline__ int corr_phase(int ph, const CUtensorMap* tm, int mat, i
         fetch_to(done + NSTG);    // refill the slots of the steps consumed so far
         const int kb = cc.kb;
         if (cc.cnt == 0) {
-            // diagonal block: columns warp, warp + 8 of V rows kb*32 .. +32 (rows past n are
-            // zero and their zero-filled tile rows keep them so)
+            // diagonal block (rows past n are zero and their zero-filled tile rows keep them so)
             const unsigned char* tile = R.buf + (size_t)((base + done) % NSTG) * TILE_BYTES;
-            constexpr int DC = (LC + CT / 32 - 1) / (CT / 32);   // columns per warp, solved side by side
-            if (warp < LC) {
-                float2 v[DC];
+            // the stored block is L_kk^{-1} (strict lower part, unit diagonal implied) over
+            // U_kk^{-1} (upper part with the diagonal): group 0 multiplies V rows kb*32 .. +32
+            // by the triangle of the phase, all rows read before any is written
+            float2 own[2];
+            if (tw == 0) {
 #pragma unroll
-                for (int d = 0; d < DC; ++d) v[d] = V[(kb * TS + lane) * LC + warp + d * (CT / 32)];
-                if (ph == PH_LOWER) {
-                    for (int jj = 0; jj + 1 < TS; ++jj) {
-                        const float2 Lv = tile_at(tile, lane, jj);
+                for (int k = 0; k < 2; ++k) {
+                    own[k] = V[(kb * TS + rr) * LC + gq + k * GW];
 #pragma unroll
-                        for (int d = 0; d < DC; ++d) {
-                            const float2 aj = shfl2(v[d], jj);
-                            if (lane > jj) ffma(v[d], make_float2(-Lv.x, -Lv.y), aj);
-                        }
-                    }
-                } else {
-                    for (int jj = TS - 1; jj >= 0; --jj) {
-                        float2 dg = tile_at(tile, jj, jj);
-                        if (dg.x == 0.f && dg.y == 0.f) dg = make_float2(1.f, 0.f);   // flagged by the factorisation
-                        const float2 Uv = tile_at(tile, lane, jj);
+                    for (int l = 0; l < TS; ++l) tk[k][l] = V[(kb * TS + l) * LC + gq + k * GW];
+                }
+            }
+            __syncthreads();
+            if (tw == 0) {
+                const unsigned char* trow = tile + rr * 128;
+                const int sw = rr & 7;
+                const bool lower = ph == PH_LOWER;
+                float2 a0[2], a1[2];
 #pragma unroll
-                        for (int d = 0; d < DC; ++d) {
-                            if (lane == jj) v[d] = fdiv(v[d], dg);
-                            const float2 aj = shfl2(v[d], jj);
-                            if (lane < jj) ffma(v[d], make_float2(-Uv.x, -Uv.y), aj);
-                        }
+                for (int k = 0; k < 2; ++k) {
+                    a0[k] = lower ? own[k] : make_float2(0.f, 0.f);
+                    a1[k] = make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int c2 = 0; c2 < TS / 2; ++c2) {
+                    float4 x = *reinterpret_cast<const float4*>(trow + (c2 >> 3) * (TILE_BYTES / 2) + (((c2 & 7) ^ sw) << 4));
+                    // columns 2 c2, 2 c2 + 1 of row rr: below the diagonal for the lower
+                    // triangle, on or above it for the upper one
+                    const bool k0 = lower ? 2 * c2 < rr : 2 * c2 >= rr, k1 = lower ? 2 * c2 + 1 < rr : 2 * c2 + 1 >= rr;
+                    if (!k0) { x.x = 0.f; x.y = 0.f; }
+                    if (!k1) { x.z = 0.f; x.w = 0.f; }
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        ffma(a0[k], make_float2(x.x, x.y), tk[k][2 * c2]);
+                        ffma(a1[k], make_float2(x.z, x.w), tk[k][2 * c2 + 1]);
                     }
                 }
 #pragma unroll
-                for (int d = 0; d < DC; ++d) V[(kb * TS + lane) * LC + warp + d * (CT / 32)] = v[d];
+                for (int k = 0; k < 2; ++k)
+                    V[(kb * TS + rr) * LC + gq + k * GW] = make_float2(a0[k].x + a1[k].x, a0[k].y + a1[k].y);
             }
         } else {
             const bool first = ph == PH_LOWER ? cc.rb0 == kb + 1 : cc.rb0 == 0;
@@ -632,6 +643,56 @@ __global__ void __launch_bounds__(CT) k_mx_correct(MixSys S, const int* __restri
             }
         }
     }
+}
+
+// Once per factorisation: the 32 x 32 diagonal blocks of every node's factors replaced by
+// their inverses, L_kk^{-1} over the strict lower part (unit diagonal implied) and
+// U_kk^{-1} over the upper part, so that the correction solves apply them as products.
+// One warp per block, lane = row; rows of the inverse by substitution against the
+// identity (row j final, then broadcast by shuffle to the rows it updates).  Rows and
+// columns of an edge block past n are the identity and are not written; a zero pivot
+// (flagged by the factorisation) counts as 1.
+__global__ void __launch_bounds__(32) k_mx_diag_inv(MixSys S) {
+    const int kb = blockIdx.x, i = blockIdx.y, e = blockIdx.z, lane = threadIdx.x;
+    const int n = S.n, r0 = kb * TS, wd = min(TS, n - r0);
+    float2* B = S.F + e * S.sF + (size_t)i * n * n + (size_t)r0 * n + r0;
+    const bool in = lane < wd;
+    float2 a[TS], x[TS];
+#pragma unroll
+    for (int c = 0; c < TS; ++c) a[c] = in && c < wd ? B[(size_t)lane * n + c] : make_float2(0.f, 0.f);
+    // L_kk^{-1}
+#pragma unroll
+    for (int c = 0; c < TS; ++c) x[c] = make_float2(c == lane ? 1.f : 0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j + 1 < TS; ++j) {
+        const float2 l = lane > j ? make_float2(-a[j].x, -a[j].y) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c <= j; ++c) ffma(x[c], l, shfl2(x[c], j));   // row j has no entries past column j
+    }
+    if (in)
+#pragma unroll
+        for (int c = 0; c < TS; ++c)
+            if (c < lane && c < wd) B[(size_t)lane * n + c] = x[c];
+    // U_kk^{-1}
+#pragma unroll
+    for (int c = 0; c < TS; ++c) x[c] = make_float2(c == lane ? 1.f : 0.f, 0.f);
+#pragma unroll
+    for (int j = TS - 1; j >= 0; --j) {
+        if (lane == j) {
+            float2 d = a[j];
+            if (d.x == 0.f && d.y == 0.f) d = make_float2(1.f, 0.f);
+            const float2 inv = fdiv(make_float2(1.f, 0.f), d);
+#pragma unroll
+            for (int c = j; c < TS; ++c) x[c] = make_float2(x[c].x * inv.x - x[c].y * inv.y, x[c].x * inv.y + x[c].y * inv.x);
+        }
+        const float2 u = lane < j ? make_float2(-a[j].x, -a[j].y) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = j; c < TS; ++c) ffma(x[c], u, shfl2(x[c], j));   // row j has no entries before column j
+    }
+    if (in)
+#pragma unroll
+        for (int c = 0; c < TS; ++c)
+            if (c >= lane && c < wd) B[(size_t)lane * n + c] = x[c];
 }
 
 // Once per factorisation: the pivot rows of node i (row j exchanged with piv[j], in
@@ -849,7 +910,8 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
     if (cgemm_tc_error(true, st)) return fail(c, PWQT_ERR_TIMEOUT, "tensor-core GEMM: a bounded mbarrier wait gave up");
     k_mx_to64<<<dim3(256, nb), NT, 0, st>>>(S);
     k_mx_perm<<<dim3(nb, N), 32, 2 * sizeof(int) * n, st>>>(S);
-    c->launches += 2;
+    k_mx_diag_inv<<<dim3((n + TS - 1) / TS, N, nb), 32, 0, st>>>(S);
+    c->launches += 3;
 
     // ---------------- refinement with FP64 residuals
     for (int b = 0; b < nb; ++b) {
