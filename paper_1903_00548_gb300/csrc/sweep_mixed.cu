@@ -31,6 +31,8 @@ namespace {
 
 constexpr int PW = 32;      // panel width
 constexpr int NT = 256;
+constexpr int MV_INTS = 4 * PW + 4;   // per energy: count, then 2 PW destination and 2 PW source rows
+constexpr int APT = 128;              // threads of the column-parallel panel kernels
 
 struct MixSys {
     int n, N, m, w;                       // w = n + m rounded up to even (16-byte rows), uniform over the batch
@@ -40,6 +42,7 @@ struct MixSys {
     int* piv; long long sP;               // per energy N x n pivot rows
     float2* XY; long long sXY;            // per energy N x n x w
     float2* Lb; long long sL;             // per energy N x n x n couplings L_i = A_{i,i-1} (node 0 unused)
+    int* mv;                              // per energy MV_INTS: the row moves of the current panel
     double2* C64; double2* R64; long long sC;   // per energy N x n x m (FP64 solution, residual)
     const SweepJob* jobs;
 };
@@ -97,9 +100,9 @@ __global__ void k_mx_form(MixSys S, int i) {
 }
 
 // ---------------------------------------------------------------- panel factorisation
-// Factor F_i[k0:n, k0:k0+wd] with partial pivoting (max |re|+|im|), apply the row
-// interchanges to the remaining columns of F_i and to XY_i, and solve the unit-lower
-// 32 x 32 block against the strip rows k0..k0+wd of [F_i right of the panel | XY_i].
+// Factor F_i[k0:n, k0:k0+wd] with partial pivoting (max |re|+|im|), one CTA per energy;
+// the row interchanges, composed into a list of row moves, and the strip solve against
+// the unit-lower 32 x 32 block go to the other columns in k_mx_panel_apply.
 __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd) {
     // the panel, column-major with an odd leading dimension: threads walk rows of one
     // column (consecutive words) in the elimination and columns of one row (odd stride,
@@ -175,10 +178,8 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
         int r = t / wd, c = t % wd;
         F[(size_t)(k0 + r) * n + k0 + c] = P[c * pld + r];
     }
-    // row interchanges on the other columns of F_i and on XY_i: the wd swaps in order
-    // compose to a permutation of at most 2 wd panel rows, moved as one gather per
-    // column (all loads of a column issued before its stores)
-    __shared__ int mv_dst[2 * PW], mv_src[2 * PW], mv_cnt;
+    // the wd swaps in order compose to a permutation of at most 2 wd panel rows: the
+    // list of moves (destination row <- source row) for k_mx_panel_apply
     if (threadIdx.x == 0) {
         int pos[2 * PW], cur[2 * PW], cnt = 0;   // panel rows touched and the original row now there
         auto slot = [&](int r) {
@@ -196,20 +197,45 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
             cur[a] = cur[b];
             cur[b] = x;
         }
+        int* mv = S.mv + (size_t)e * MV_INTS;
         int k = 0;
         for (int q = 0; q < cnt; ++q)
-            if (cur[q] != pos[q]) { mv_dst[k] = pos[q]; mv_src[k] = cur[q]; ++k; }
-        mv_cnt = k;
+            if (cur[q] != pos[q]) { mv[1 + k] = pos[q]; mv[1 + 2 * PW + k] = cur[q]; ++k; }
+        mv[0] = k;
     }
+    if (threadIdx.x == 0 && st) atomicOr(S.jobs[e].status, st);
+}
+
+// The panel's row moves on the other columns of F_i and on XY_i (one column per thread,
+// all loads of a column issued before its stores), then the strip rows k0..k0+wd of
+// [F right of the panel | XY] <- L11^{-1} strip (unit lower, L11 from the factored panel).
+// Grid (column chunks of APT, energies): the columns are independent.
+__global__ void __launch_bounds__(APT) k_mx_panel_apply(MixSys S, int i, int k0, int wd) {
+    __shared__ float2 L11[PW][PW + 1];
+    __shared__ int mv_dst[2 * PW], mv_src[2 * PW], mv_cnt;
+    const int e = blockIdx.y;
+    const int n = S.n, w = S.w;
+    float2* F = S.F + e * S.sF + (size_t)i * n * n;
+    float2* XY = S.XY + e * S.sXY + (size_t)i * n * w;
+    const int* mv = S.mv + (size_t)e * MV_INTS;
+    for (int t = threadIdx.x; t < PW * PW; t += APT) {
+        const int r = t / PW, c = t % PW;
+        L11[r][c] = (r < wd && c < r) ? F[(size_t)(k0 + r) * n + k0 + c] : make_float2(0.f, 0.f);
+    }
+    if (threadIdx.x == 0) mv_cnt = mv[0];
+    if (threadIdx.x < 2 * PW) { mv_dst[threadIdx.x] = mv[1 + threadIdx.x]; mv_src[threadIdx.x] = mv[1 + 2 * PW + threadIdx.x]; }
     __syncthreads();
     const int nmv = mv_cnt;
     const int ncolF = n - wd;
-    for (int c = threadIdx.x; c < ncolF + w; c += NT) {
-        float2* base;
-        size_t ld;
-        if (c < ncolF) { base = F + (c < k0 ? c : c + wd); ld = n; }
-        else { base = XY + (c - ncolF); ld = w; }
-        base += (size_t)k0 * ld;
+    const int c = blockIdx.x * APT + threadIdx.x;
+    if (c >= ncolF + w) return;
+    float2* base;
+    size_t ld;
+    bool right;
+    if (c < ncolF) { base = F + (c < k0 ? c : c + wd); ld = n; right = c >= k0; }
+    else { base = XY + (c - ncolF); ld = w; right = true; }
+    base += (size_t)k0 * ld;
+    {
         float2 v[2 * PW];
 #pragma unroll
         for (int q = 0; q < 2 * PW; ++q)
@@ -218,50 +244,39 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
         for (int q = 0; q < 2 * PW; ++q)
             if (q < nmv) base[(size_t)mv_dst[q] * ld] = v[q];
     }
-    __syncthreads();
-    // strip: rows k0..k0+wd of [F cols k0+wd..n | XY] <- L11^{-1} strip (unit lower)
-    const int right = n - k0 - wd;
-    for (int c = threadIdx.x; c < right + w; c += NT) {
-        float2 x[PW];
-        float2* base;
-        size_t ld;
-        if (c < right) { base = F + (size_t)k0 * n + k0 + wd + c; ld = n; }
-        else { base = XY + (size_t)k0 * w + (c - right); ld = w; }
+    if (!right) return;
+    float2 x[PW];
 #pragma unroll
-        for (int j = 0; j < PW; ++j) x[j] = j < wd ? base[(size_t)j * ld] : make_float2(0.f, 0.f);
+    for (int j = 0; j < PW; ++j) x[j] = j < wd ? base[(size_t)j * ld] : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int j = 1; j < PW; ++j) {
-            if (j < wd) {
-                float2 s = x[j];
+    for (int j = 1; j < PW; ++j) {
+        float2 s = x[j];
 #pragma unroll
-                for (int l = 0; l < PW; ++l)
-                    if (l < j) {
-                        float2 L = P[l * pld + j];
-                        ffma(s, make_float2(-L.x, -L.y), x[l]);
-                    }
-                x[j] = s;
+        for (int l = 0; l < PW; ++l)
+            if (l < j) {
+                const float2 L = L11[j][l];
+                ffma(s, make_float2(-L.x, -L.y), x[l]);
             }
-        }
-#pragma unroll
-        for (int j = 0; j < PW; ++j)
-            if (j < wd) base[(size_t)j * ld] = x[j];
+        x[j] = s;
     }
-    if (threadIdx.x == 0 && st) atomicOr(S.jobs[e].status, st);
+#pragma unroll
+    for (int j = 0; j < PW; ++j)
+        if (j < wd) base[(size_t)j * ld] = x[j];
 }
 
 // XY_i[k0:k0+wd, :] <- U11^{-1} XY_i[k0:k0+wd, :]
-__global__ void __launch_bounds__(NT) k_mx_trsm_up(MixSys S, int i, int k0, int wd) {
+__global__ void __launch_bounds__(APT) k_mx_trsm_up(MixSys S, int i, int k0, int wd) {
     __shared__ float2 U[PW][PW + 1];
-    const int e = blockIdx.x;
+    const int e = blockIdx.y;
     const int n = S.n, w = S.w;
     const float2* F = S.F + e * S.sF + (size_t)i * n * n;
     float2* XY = S.XY + e * S.sXY + (size_t)i * n * w;
-    for (int t = threadIdx.x; t < PW * PW; t += NT) {
+    for (int t = threadIdx.x; t < PW * PW; t += APT) {
         int r = t / PW, c = t % PW;
         U[r][c] = (r < wd && c < wd) ? F[(size_t)(k0 + r) * n + k0 + c] : make_float2(r == c ? 1.f : 0.f, 0.f);
     }
     __syncthreads();
-    for (int c = threadIdx.x; c < w; c += NT) {
+    for (int c = blockIdx.x * APT + threadIdx.x; c < w; c += gridDim.x * APT) {
         float2 x[PW];
         float2* base = XY + (size_t)k0 * w + c;
 #pragma unroll
@@ -762,7 +777,7 @@ int corr_error_flag(bool reset, cudaStream_t st) {
 size_t mixed_bytes_per_energy(int n, int N, int m) {
     // F + XY + L_i (complex64) + pivots + FP64 solution and residual
     const size_t w = (size_t)n + m + (m & 1);
-    return sizeof(float2) * ((size_t)N * n * n + (size_t)N * n * w + (size_t)N * n * n) + sizeof(int) * (size_t)N * n +
+    return sizeof(float2) * ((size_t)N * n * n + (size_t)N * n * w + (size_t)N * n * n) + sizeof(int) * ((size_t)N * n + MV_INTS) + 256 +
            3 * sizeof(double2) * (size_t)N * n * m +     // FP64 solution, residual, float-float copy
            2 * oz::panel_item_bytes(n, 1) +               // self-energy slice panels
            oz::b_bytes(n, N, m + 32);                     // solution slices (a column tile of slack)
@@ -830,6 +845,7 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
     S.XY = (float2*)take(sizeof(float2) * S.sXY * nb);
     S.Lb = (float2*)take(sizeof(float2) * S.sL * nb);
     S.piv = (int*)take(sizeof(int) * S.sP * nb);
+    S.mv = (int*)take(sizeof(int) * MV_INTS * nb);
     S.C64 = (double2*)take(sizeof(double2) * S.sC * nb);
     S.R64 = (double2*)take(sizeof(double2) * S.sC * nb);
     float4* Cff = (float4*)take(sizeof(float4) * S.sC * nb);
@@ -877,7 +893,8 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         for (int k0 = 0; k0 < n; k0 += PW) {
             const int wd = std::min(PW, n - k0);
             k_mx_panel<<<nb, NT, sizeof(float2) * (size_t)((n - k0) | 1) * PW, st>>>(S, i, k0, wd);
-            c->launches++;
+            k_mx_panel_apply<<<dim3((n - wd + w + APT - 1) / APT, nb), APT, 0, st>>>(S, i, k0, wd);
+            c->launches += 2;
             const int rest = n - k0 - wd;
             if (rest > 0)
                 gemm(Fi + (size_t)(k0 + wd) * n + k0, S.sF, n, Fi + (size_t)k0 * n + k0 + wd, S.sF, n, XYi + (size_t)k0 * w, S.sXY, w,
@@ -885,7 +902,7 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         }
         for (int k0 = ((n - 1) / PW) * PW; k0 >= 0; k0 -= PW) {
             const int wd = std::min(PW, n - k0);
-            k_mx_trsm_up<<<nb, NT, 0, st>>>(S, i, k0, wd);
+            k_mx_trsm_up<<<dim3((w + APT - 1) / APT, nb), APT, 0, st>>>(S, i, k0, wd);
             c->launches++;
             if (k0 > 0) gemm(Fi + k0, S.sF, n, XYi + (size_t)k0 * w, S.sXY, w, XYi + (size_t)k0 * w, S.sXY, w, XYi, S.sXY, w, XYi, S.sXY,
                              w, w, k0, w, wd);
