@@ -261,6 +261,15 @@ int pwqt_profile_refinement(pwqt_ctx* ctx, double* residual_ms, double* correcti
  * slice products, and the launch count.  Any pointer may be NULL.
  */
 int pwqt_profile_residual(pwqt_ctx* ctx, double* ms, double* cmacs, double* mma_flops, long long* launches);
+/*
+ * Correction solves of the mixed path recorded while pwqt_profile is enabled (same
+ * reset; the paper has no counterpart): CUDA-event milliseconds of the correction
+ * launches (summed over the halves of a mixed batch, the same figure as the correction
+ * time of pwqt_profile_refinement), the method's complex multiply-adds (3 N n^2 per
+ * refining column: the products with L_i and X_i and the two triangular solves), and
+ * the launch count.  Any pointer may be NULL.
+ */
+int pwqt_profile_correction(pwqt_ctx* ctx, double* ms, double* cmacs, long long* launches);
 
 #define PWQT_RESIDUAL_SLICED       0
 #define PWQT_RESIDUAL_FLOAT_FLOAT  1

@@ -290,6 +290,7 @@ int pwqt_profile(pwqt_ctx* c, int enable, double* sweep_ms, long long* sweep_lau
         c->prof_ms = 0; c->prof_launches = 0; c->prof_flops = 0;
         c->prof_phase_ms[0] = c->prof_phase_ms[1] = 0; c->prof_ir_iters = 0;
         c->prof_oz_ms = c->prof_oz_cmacs = c->prof_oz_mma_flops = 0; c->prof_oz_launches = 0;
+        c->prof_corr_cmacs = 0; c->prof_corr_launches = 0;
     }
     return PWQT_OK;
 }
@@ -404,6 +405,14 @@ int pwqt_profile_residual(pwqt_ctx* c, double* ms, double* cmacs, double* mma_fl
     if (cmacs) *cmacs = c->prof_oz_cmacs;
     if (mma_flops) *mma_flops = c->prof_oz_mma_flops;
     if (launches) *launches = c->prof_oz_launches;
+    return PWQT_OK;
+}
+
+int pwqt_profile_correction(pwqt_ctx* c, double* ms, double* cmacs, long long* launches) {
+    PWQT_TRY(check_ctx(c));
+    if (ms) *ms = c->prof_phase_ms[1];
+    if (cmacs) *cmacs = c->prof_corr_cmacs;
+    if (launches) *launches = c->prof_corr_launches;
     return PWQT_OK;
 }
 

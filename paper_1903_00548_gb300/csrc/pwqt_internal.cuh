@@ -141,6 +141,9 @@ struct Lane {
     // bf16 MMA flops issued for the 34 kept slice pairs, launches
     double prof_oz_ms = 0, prof_oz_cmacs = 0, prof_oz_mma_flops = 0;
     long long prof_oz_launches = 0;
+    // correction solves: the method's complex MACs (3 N n^2 per refining column), launches
+    double prof_corr_cmacs = 0;
+    long long prof_corr_launches = 0;
     int init(int dev);      // stream and events on first use
     void destroy();
 };
@@ -189,6 +192,8 @@ struct pwqt_ctx {
     long long prof_ir_iters = 0;
     double prof_oz_ms = 0, prof_oz_cmacs = 0, prof_oz_mma_flops = 0;
     long long prof_oz_launches = 0;
+    double prof_corr_cmacs = 0;
+    long long prof_corr_launches = 0;
     cudaEvent_t ev2 = nullptr, ev3 = nullptr;
     // host threads that fill the contact cache concurrently
     int lead_threads = 8;

@@ -367,6 +367,8 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
                 c->prof_phase_ms[0] += L.prof_phase_ms[0]; c->prof_phase_ms[1] += L.prof_phase_ms[1];
                 c->prof_oz_ms += L.prof_oz_ms; c->prof_oz_cmacs += L.prof_oz_cmacs;
                 c->prof_oz_mma_flops += L.prof_oz_mma_flops; c->prof_oz_launches += L.prof_oz_launches;
+                c->prof_corr_cmacs += L.prof_corr_cmacs; c->prof_corr_launches += L.prof_corr_launches;
+                L.prof_corr_cmacs = 0; L.prof_corr_launches = 0;
                 it_max = std::max(it_max, L.prof_ir_iters);
                 L.prof_ms = L.prof_flops = L.prof_phase_ms[0] = L.prof_phase_ms[1] = 0;
                 L.prof_oz_ms = L.prof_oz_cmacs = L.prof_oz_mma_flops = 0;

@@ -1122,6 +1122,15 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         }
         PWQT_CUDA(c, cudaMemcpyAsync(active_d, active.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
         const int ck = corr_pick(active), lc = corr_lcs[ck];
+        if (c->profile) {
+            // the method's work: per refining column and node the products with L_i and X_i
+            // and the two triangular solves, n^2 complex MACs each of the three
+            double cols = 0;
+            for (int b = 0; b < nb; ++b)
+                if (active[b]) cols += jobs[b].ms + jobs[b].md;
+            L.prof_corr_cmacs += 3.0 * N * (double)n * n * cols;
+            L.prof_corr_launches += 1;
+        }
         const dim3 cgrid(nb, (m + lc - 1) / lc);
         const size_t csm = correct_smem(n, lc);
         if (lc == 16) k_mx_correct<16><<<cgrid, CT, csm, st>>>(S, active_d, tmL, tmF, tmX);

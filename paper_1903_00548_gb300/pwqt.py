@@ -28,7 +28,7 @@ EXPORTS = ["pwqt_create", "pwqt_destroy", "pwqt_last_error", "pwqt_assemble_intr
            "pwqt_get_blocks", "pwqt_set_extrinsic", "pwqt_solve", "pwqt_solve_dev", "pwqt_prepare_leads",
            "pwqt_cache_info", "pwqt_bands", "pwqt_kernel_launches", "pwqt_profile", "pwqt_solve_noalloc", "pwqt_cgemm_c64",
            "pwqt_density_reset", "pwqt_accumulate_density", "pwqt_get_density_matrix", "pwqt_density_grid",
-           "pwqt_profile_refinement", "pwqt_set_refinement", "pwqt_set_residual", "pwqt_profile_residual", "pwqt_solve_multi",
+           "pwqt_profile_refinement", "pwqt_set_refinement", "pwqt_set_residual", "pwqt_profile_residual", "pwqt_profile_correction", "pwqt_solve_multi",
            "pwqt_server_create", "pwqt_server_add_basis", "pwqt_server_submit", "pwqt_server_wait",
            "pwqt_server_stats", "pwqt_server_batch_stats", "pwqt_server_last_error", "pwqt_server_destroy", "pwqt_integrate",
            "pwqt_transmission_caroli", "pwqt_self_consistent", "pwqt_green_diagonal"]
@@ -106,6 +106,7 @@ def load(path: str = LIB_PATH):
     lib.pwqt_set_refinement.argtypes = [P, D, I]
     lib.pwqt_set_residual.argtypes = [P, I]
     lib.pwqt_profile_residual.argtypes = [P, dp, dp, dp, C.POINTER(C.c_longlong)]
+    lib.pwqt_profile_correction.argtypes = [P, dp, dp, C.POINTER(C.c_longlong)]
     lib.pwqt_solve_multi.argtypes = [P, I, ip, I, dp, I, dp, dp, dp, ip, dp, dp, ip, ip]
     lib.pwqt_server_create.argtypes = [C.POINTER(P), C.POINTER(ServerOpts)]
     lib.pwqt_server_add_basis.argtypes = [P, I, C.POINTER(CellC), C.POINTER(FormFactorC), D, I, ip]
@@ -410,6 +411,13 @@ class Context:
         n = C.c_longlong()
         self._check(self.lib.pwqt_profile_residual(self.h, C.byref(ms), C.byref(cm), C.byref(fl), C.byref(n)))
         return ms.value, cm.value, fl.value, n.value
+
+    def profile_correction(self):
+        """(ms, complex MACs, launches) of the correction solves recorded while profiling."""
+        ms, cm = C.c_double(), C.c_double()
+        n = C.c_longlong()
+        self._check(self.lib.pwqt_profile_correction(self.h, C.byref(ms), C.byref(cm), C.byref(n)))
+        return ms.value, cm.value, n.value
 
     def profile_refinement(self):
         """(residual ms, correction ms, refinement iterations) recorded while profiling."""
