@@ -457,8 +457,8 @@ def run_ours(args, world, rank, local):
                              "(products with L_i and X_i, the two triangular solves)",
                      "peak_source": f"FP32 FMA: {sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz", "traffic": None,
                      "ms_per_step": cor_ms, "launches": cor_launches,
-                     "note": "event time of each lane's launches; the two lanes' launches share the SMs, "
-                             "so the per-launch time includes the other lane's work"}
+                     "note": "event time of the launches in the profiled step, whose two halves run one "
+                             "after the other"}
     # the roofline object: the single kernel with the largest event time per step among the
     # refinement kernels; the block sweep (several kernels per panel) is reported beside it
     singles = {"residual": (oz_ms, roof_res), "correction": (cor_ms, roof_corr)}
@@ -487,8 +487,9 @@ def run_ours(args, world, rank, local):
             "roofline_residual": roof_res, "roofline_correction": roof_corr, "density": dens,
             "phases_ms_per_step": {"sweep": sweep_ms, "refine_residual": ir_res_ms, "refine_correction": ir_cor_ms,
                                    "refine_iterations": ir_iters, "profiled_step_ms": prof_ms,
-                                   "note": "one extra step with CUDA events, after the timed steps; the two halves "
-                                           "of the batch run on two streams, so phase sums can exceed the step"},
+                                   "note": "one extra step with CUDA events, after the timed steps; its two halves "
+                                           "run one after the other (the timed steps overlap them on two streams), "
+                                           "so each kernel's event time is its own; profiled_step_ms is that step"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "results": {"max_resid": float(np.max(resid)), "max_iters": int(np.max(iters)),
                         "status_nonzero": int(np.count_nonzero(status)),

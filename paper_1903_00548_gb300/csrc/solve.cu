@@ -342,25 +342,34 @@ int solve_batch(pwqt_ctx* c, System& s, int nE, const double* E, int precision, 
             PWQT_TRY(c->lanes[0].init(c->dev) == PWQT_OK ? PWQT_OK : fail(c, PWQT_ERR_CUDA, "lane stream"));
             if (nb >= 16) {
                 // two halves on two lanes (streams, host threads): the GPU runs one half's
-                // float-float residual beside the other half's latency-bound kernels
+                // residual and correction launches beside the other half's latency-bound sweep
+                // kernels.  While profiling, the halves run one after the other, so that each
+                // kernel's event time is its own and not the other lane's work on shared SMs.
                 PWQT_TRY(c->lanes[1].init(c->dev) == PWQT_OK ? PWQT_OK : fail(c, PWQT_ERR_CUDA, "lane stream"));
                 split = nb / 2;
                 PWQT_CUDA(c, cudaStreamSynchronize(st));   // work the halves depend on (zero block)
                 int rc_b = PWQT_OK;
-                std::thread tb([&] {
+                auto run_b = [&] {
                     cudaSetDevice(c->dev);
                     rc_b = group(e0 + split, nb - split, &c->lanes[1], c->lanes[1].st, obs_b);
-                });
-                const int rc_a = group(e0, split, &c->lanes[0], c->lanes[0].st, obs_a);
-                tb.join();
+                };
+                int rc_a;
+                if (c->profile) {
+                    rc_a = group(e0, split, &c->lanes[0], c->lanes[0].st, obs_a);
+                    if (rc_a == PWQT_OK) run_b();
+                } else {
+                    std::thread tb(run_b);
+                    rc_a = group(e0, split, &c->lanes[0], c->lanes[0].st, obs_a);
+                    tb.join();
+                }
                 PWQT_TRY(rc_a);
                 PWQT_TRY(rc_b);
             } else {
                 PWQT_TRY(group(e0, nb, &c->lanes[0], st, obs_a));
             }
             // the lanes' profile counters into the context's: times, flops and launches add up
-            // (per-lane rates stay per launch); the halves refine in parallel, so a batch counts
-            // the larger of their iteration counts
+            // (per-lane rates stay per launch); a batch counts the larger of the halves'
+            // iteration counts
             long long it_max = 0;
             for (auto& L : c->lanes) {
                 c->prof_ms += L.prof_ms; c->prof_flops += L.prof_flops; c->prof_launches += L.prof_launches;
