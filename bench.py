@@ -294,7 +294,11 @@ def run_ours(args, world, rank, local):
         wl.U = W.random_smooth(args.nodes)
     prec_name = "mixed" if args.precision == "auto" else args.precision
     prec = pw.MIXED if prec_name == "mixed" else pw.FP64
-    batch = args.batch or (32 if prec == pw.MIXED else 152)
+    batch = args.batch
+    if not batch and prec == pw.MIXED and not args.nodes:
+        from paper_1903_00548_gb300 import autotune
+        batch = autotune.lookup(args.workload, 2 * wl.n_bands, wl.n_nodes, "mixed") or 0
+    batch = batch or (32 if prec == pw.MIXED else 152)
     n_grid = len(wl.energies)
     E = shard_energies(wl.energies, batch, rank, world)
 
