@@ -112,9 +112,8 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
     __shared__ float bv[NT / 32];
     __shared__ int bi[NT / 32];
     const int e = blockIdx.x;
-    const int n = S.n, w = S.w, rows = n - k0, pld = rows | 1;   // panel leading dimension (odd)
+    const int n = S.n, rows = n - k0, pld = rows | 1;   // panel leading dimension (odd)
     float2* F = S.F + e * S.sF + (size_t)i * n * n;
-    float2* XY = S.XY + e * S.sXY + (size_t)i * n * w;
     int* piv = S.piv + e * S.sP + (size_t)i * n;
     int st = 0;
 #pragma unroll 8
@@ -178,32 +177,165 @@ __global__ void __launch_bounds__(NT) k_mx_panel(MixSys S, int i, int k0, int wd
         int r = t / wd, c = t % wd;
         F[(size_t)(k0 + r) * n + k0 + c] = P[c * pld + r];
     }
-    // the wd swaps in order compose to a permutation of at most 2 wd panel rows: the
-    // list of moves (destination row <- source row) for k_mx_panel_apply
-    if (threadIdx.x == 0) {
-        int pos[2 * PW], cur[2 * PW], cnt = 0;   // panel rows touched and the original row now there
-        auto slot = [&](int r) {
-            for (int q = 0; q < cnt; ++q)
-                if (pos[q] == r) return q;
-            pos[cnt] = r;
-            cur[cnt] = r;
-            return cnt++;
-        };
+    // the wd swaps in order, as a map panel row -> original row (in the panel's shared
+    // memory, free after the write-back); rows with a new origin (at most 2 wd) become
+    // the list of moves (destination row <- source row) for k_mx_panel_apply
+    __shared__ int mvc;
+    int* orig = reinterpret_cast<int*>(P);
+    __syncthreads();
+    for (int r = threadIdx.x; r < rows; r += NT) orig[r] = r;
+    if (threadIdx.x == 0) mvc = 0;
+    __syncthreads();
+    if (threadIdx.x == 0)
         for (int j = 0; j < wd; ++j) {
             const int p = prow[j];
-            if (p == j) continue;
-            const int a = slot(j), b = slot(p);
-            const int x = cur[a];
-            cur[a] = cur[b];
-            cur[b] = x;
+            if (p != j) { const int x = orig[j]; orig[j] = orig[p]; orig[p] = x; }
         }
-        int* mv = S.mv + (size_t)e * MV_INTS;
-        int k = 0;
-        for (int q = 0; q < cnt; ++q)
-            if (cur[q] != pos[q]) { mv[1 + k] = pos[q]; mv[1 + 2 * PW + k] = cur[q]; ++k; }
-        mv[0] = k;
+    __syncthreads();
+    int* mv = S.mv + (size_t)e * MV_INTS;
+    for (int r = threadIdx.x; r < rows; r += NT)
+        if (orig[r] != r) {
+            const int k = atomicAdd(&mvc, 1);
+            mv[1 + k] = r;
+            mv[1 + 2 * PW + k] = orig[r];
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mv[0] = mvc;
+        if (st) atomicOr(S.jobs[e].status, st);
     }
-    if (threadIdx.x == 0 && st) atomicOr(S.jobs[e].status, st);
+}
+
+// k_mx_panel for panels of at most 512 rows: the panel in registers (thread t holds panel
+// rows t and t + 256, all 32 columns), so the rank-1 updates touch no shared memory; per
+// column the pivot (max |re|+|im|, the lower row on ties, as k_mx_panel) is found by warp
+// shuffles and one pass over the warps' candidates, and rows j and p are exchanged and
+// the pivot row broadcast through shared memory.  Pivots, the factored panel and the list
+// of row moves are written as k_mx_panel writes them.
+constexpr int PR_NT = 256;
+__global__ void __launch_bounds__(PR_NT) k_mx_panel_reg(MixSys S, int i, int k0, int wd) {
+    __shared__ float2 prow_s[PW], jrow_s[PW];
+    __shared__ float bv[PR_NT / 32];
+    __shared__ int bi[PR_NT / 32], prow[PW], sel;
+    const int e = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int n = S.n, rows = n - k0;
+    float2* F = S.F + e * S.sF + (size_t)i * n * n + (size_t)k0 * n + k0;   // panel origin, row stride n
+    int* piv = S.piv + e * S.sP + (size_t)i * n;
+    float2 a[2][PW];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int r = t + q * PR_NT;
+#pragma unroll
+        for (int c = 0; c < PW; ++c) a[q][c] = (r < rows && c < wd) ? F[(size_t)r * n + c] : make_float2(0.f, 0.f);
+    }
+    int st = 0;
+#pragma unroll
+    for (int j = 0; j < PW; ++j) {
+        if (j >= wd) break;
+        float best = -1.f;
+        int idx = j;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int r = t + q * PR_NT;
+            if (r >= j && r < rows) {
+                const float v = fabsf(a[q][j].x) + fabsf(a[q][j].y);
+                if (v > best) { best = v; idx = r; }
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_down_sync(0xffffffffu, best, o);
+            const int oi = __shfl_down_sync(0xffffffffu, idx, o);
+            if (ov > best || (ov == best && oi < idx)) { best = ov; idx = oi; }
+        }
+        if (lane == 0) { bv[warp] = best; bi[warp] = idx; }
+        __syncthreads();
+        if (t == 0) {
+            float b = bv[0];
+            int ii = bi[0];
+            for (int q = 1; q < PR_NT / 32; ++q)
+                if (bv[q] > b || (bv[q] == b && bi[q] < ii)) { b = bv[q]; ii = bi[q]; }
+            const int p = b < 0.f ? j : ii;   // no candidate rows: keep the diagonal
+            sel = p;
+            prow[j] = p;
+            piv[k0 + j] = k0 + p;
+        }
+        __syncthreads();
+        const int p = sel;
+        // the owners publish row p (the pivot row) and, if different, row j
+        if (t == p % PR_NT) {
+            const bool hi = p >= PR_NT;
+#pragma unroll
+            for (int c = 0; c < PW; ++c) prow_s[c] = hi ? a[1][c] : a[0][c];
+        }
+        if (p != j && t == j) {
+#pragma unroll
+            for (int c = 0; c < PW; ++c) jrow_s[c] = a[0][c];
+        }
+        __syncthreads();
+        if (p != j) {
+            if (t == j)
+#pragma unroll
+                for (int c = 0; c < PW; ++c) a[0][c] = prow_s[c];
+            if (t == p % PR_NT) {
+                if (p >= PR_NT) {
+#pragma unroll
+                    for (int c = 0; c < PW; ++c) a[1][c] = jrow_s[c];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < PW; ++c) a[0][c] = jrow_s[c];
+                }
+            }
+        }
+        float2 pv = prow_s[j];
+        if (pv.x == 0.f && pv.y == 0.f) { st |= PWQT_ST_SINGULAR_PIVOT; pv = make_float2(1.f, 0.f); }
+        const float2 inv = fdiv(make_float2(1.f, 0.f), pv);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int r = t + q * PR_NT;
+            if (r > j && r < rows) {
+                const float2 x = a[q][j];
+                const float2 l = make_float2(x.x * inv.x - x.y * inv.y, x.x * inv.y + x.y * inv.x);
+                a[q][j] = l;
+#pragma unroll
+                for (int c = j + 1; c < PW; ++c) {
+                    const float2 u = prow_s[c];
+                    ffma(a[q][c], make_float2(-l.x, -l.y), u);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int r = t + q * PR_NT;
+        if (r < rows)
+#pragma unroll
+            for (int c = 0; c < PW; ++c)
+                if (c < wd) F[(size_t)r * n + c] = a[q][c];
+    }
+    // the swaps in order, as a map panel row -> original row; rows with a new origin (at
+    // most 2 wd) become the move list
+    __shared__ int orig[2 * PR_NT], mvc;
+    for (int r = t; r < rows; r += PR_NT) orig[r] = r;
+    if (t == 0) mvc = 0;
+    __syncthreads();
+    if (t == 0)
+        for (int j = 0; j < wd; ++j) {
+            const int p = prow[j];
+            if (p != j) { const int x = orig[j]; orig[j] = orig[p]; orig[p] = x; }
+        }
+    __syncthreads();
+    int* mv = S.mv + (size_t)e * MV_INTS;
+    for (int r = t; r < rows; r += PR_NT)
+        if (orig[r] != r) {
+            const int k = atomicAdd(&mvc, 1);
+            mv[1 + k] = r;
+            mv[1 + 2 * PW + k] = orig[r];
+        }
+    __syncthreads();
+    if (t == 0) {
+        mv[0] = mvc;
+        if (st) atomicOr(S.jobs[e].status, st);
+    }
 }
 
 // The panel's row moves on the other columns of F_i and on XY_i (one column per thread,
@@ -348,14 +480,8 @@ size_t correct_smem(int n, int lc) {
            sizeof(float2) * 2 * np * lc;
 }
 
-// element (r, c) of a ring tile: half c / 16 holds 32 rows of 128 bytes whose 16-byte
-// chunks are permuted by the 128-byte swizzle (chunk ^ (r % 8))
-__device__ __forceinline__ int tile_off(int r, int c) {
-    return (c >> 4) * (TILE_BYTES / 2) + r * 128 + ((((c & 15) >> 1) ^ (r & 7)) << 4) + ((c & 1) << 3);
-}
-__device__ __forceinline__ float2 tile_at(const unsigned char* tile, int r, int c) {
-    return *reinterpret_cast<const float2*>(tile + tile_off(r, c));
-}
+// A ring tile is two halves (columns 0-15, 16-31) of 32 rows of 128 bytes whose 16-byte
+// chunks are permuted by the 128-byte swizzle: chunk c of row r sits at chunk c ^ (r % 8).
 
 __device__ __forceinline__ float2 shfl2(float2 v, int src) {
     return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
@@ -439,7 +565,7 @@ __device__ __noinline__ int corr_phase(int ph, const CUtensorMap* tm, int mat, i
     constexpr int TPS = corr_tps(LC), NSTG = corr_nstg(LC);
     constexpr int GW = LC / 2, TG = CT / TPS;
     static_assert(TG == TS * GW, "a group: 32 rows x GW column pairs");
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int t = threadIdx.x;
     const int tw = t / TG, gq = t % GW, rr = (t % TG) / GW;
     const int nbk = (n + TS - 1) / TS;
     const int ntiles = ph == PH_SCHUR ? nbk * nbk : nbk * (nbk + 1) / 2;
@@ -892,7 +1018,8 @@ int solve_mixed(pwqt_ctx* c, System& s, const SweepSys& sys, std::vector<SweepJo
         }
         for (int k0 = 0; k0 < n; k0 += PW) {
             const int wd = std::min(PW, n - k0);
-            k_mx_panel<<<nb, NT, sizeof(float2) * (size_t)((n - k0) | 1) * PW, st>>>(S, i, k0, wd);
+            if (n - k0 <= 2 * PR_NT) k_mx_panel_reg<<<nb, PR_NT, 0, st>>>(S, i, k0, wd);
+            else k_mx_panel<<<nb, NT, sizeof(float2) * (size_t)((n - k0) | 1) * PW, st>>>(S, i, k0, wd);
             k_mx_panel_apply<<<dim3((n - wd + w + APT - 1) / APT, nb), APT, 0, st>>>(S, i, k0, wd);
             c->launches += 2;
             const int rest = n - k0 - wd;
