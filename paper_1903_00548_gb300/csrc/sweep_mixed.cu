@@ -450,14 +450,13 @@ __global__ void k_mx_to64(MixSys S) {
 //   backward  d_{N-1} = w_{N-1},  d_i = w_i - X_i d_{i+1},  c_i += d_i (FP64)
 // with L_i the stored coupling A_{i,i-1}, F_i = P_i^T L_i U_i the node's LU factors
 // and X_i the y-free columns of XY_i.  The CTA's two n x LC work vectors live in shared
-// memory; the matrices stream through it in 32 x 32 tiles (cp.async ring NSTG deep,
-// two 16-byte pieces per thread and tile); a tile updates 32 rows x LC columns with
-// the multiplicand's values in registers.
+// memory; the matrices stream through the rest of it in 32 x 32 tiles (tensor-map copies
+// into a ring of mbarrier-tracked slots); a tile updates 32 rows x LC columns with the
+// multiplicand's values in registers.  The 32 x 32 diagonal blocks of the triangular
+// factors hold their inverses (k_mx_diag_inv), so they are tile products too.
 // LC is picked per refinement step from the columns still refining: 16 while most
 // energies refine (fewest tile reads per column), down to 2 for the last few, where
 // the length of one CTA's chain through the nodes is the step's time.
-// The 32 x 32 diagonal blocks of the triangular factors are solved one column per
-// warp (lane = row, the solved value broadcast by shuffle).
 constexpr int TS = 32;     // tile edge
 constexpr int CT = 256;    // threads of a correction CTA
 constexpr int TILE_BYTES = TS * TS * 8;   // two 128-byte-swizzled halves of 32 rows x 16 complex64
