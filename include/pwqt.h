@@ -215,27 +215,29 @@ int pwqt_bands(pwqt_ctx* ctx, int n_k, const double* k, double* E_out);
 
 /*
  * CUDA-event timing of the block-sweep kernels (the dominant cost, Sec. 3.2
- * system): with enable != 0 every sweep launch is bracketed by events on the
- * stream it runs on and its duration is accumulated.  Outputs (any may be NULL):
- * total milliseconds, number of timed launches, and the algorithmic flops of those
- * launches, (56/3) N n^3 real flops per energy (complex LU 8/3 n^3 + solve for
+ * system): with enable != 0 the block sweep of every batch (all its node and panel
+ * launches) is bracketed by events on the stream it runs on and its duration is
+ * accumulated.  Outputs (any may be NULL): total milliseconds, number of timed
+ * sweeps, and their algorithmic flops, (56/3) N n^3 real flops per energy (complex LU 8/3 n^3 + solve for
  * X_i 8 n^3 + Schur product 8 n^3 per node).  reset != 0 zeroes the counters after
- * reading them.  Timing serialises the host with each sweep launch.
+ * reading them.  Timing serialises the host with each sweep launch, and a mixed
+ * batch that otherwise runs as two halves on two streams runs them one after the
+ * other while timing is enabled, so that each launch's event time is its own.
  */
 int pwqt_profile(pwqt_ctx* ctx, int enable, double* sweep_ms, long long* sweep_launches,
                  double* sweep_flops, int reset);
 
 /*
  * Change the refinement stopping rule of the mixed path for later solves (the
- * pwqt_opts fields ir_tol and ir_max_iters; 0 selects the defaults 1e-9 and 40).
+ * pwqt_opts fields ir_tol and ir_max_iters; 0 selects the defaults 1e-10 and 40).
  * Errors: PWQT_ERR_INVALID_ARG for a negative or non-finite value.
  */
 int pwqt_set_refinement(pwqt_ctx* ctx, double ir_tol, int ir_max_iters);
 
 /*
  * Refinement phases of the mixed path recorded while pwqt_profile is enabled
- * (same reset): total milliseconds of the residual evaluations (float-float
- * B - A c, Sec. 3.2 system) and of the correction solves with the stored
+ * (same reset): total milliseconds of the residual evaluations (B - A c, Sec. 3.2
+ * system, of the kind set by pwqt_set_residual) and of the correction solves with the stored
  * complex64 factors, and the number of batched refinement iterations.  Any
  * pointer may be NULL.
  */
